@@ -1,0 +1,212 @@
+/*
+ * cpm.h -- C ABI of the GB300 (sm_103a) closest point method library with
+ * interior boundary conditions.
+ *
+ * The library implements the discrete CPM of King, Su, Aanjaneya, Ruuth and
+ * Batty, "A Closest Point Method for PDEs on Manifolds with Interior Boundary
+ * Conditions for Geometry Processing" (ACM TOG 2024): a narrow band of grid
+ * nodes around a manifold S (Eq. 3, Alg. 1), duplicated BC degrees of freedom
+ * near interior boundaries C (Sec. 4.1), interpolation and finite-difference
+ * stencils restricted to the correct side of C by the closest-point crossing
+ * test (Eqs. 8-11), and the system
+ *
+ *     A = m I + n [ diag(L) + (L - diag L) E ]          (Sec. 5.3-5.4)
+ *
+ * applied matrix-free and solved with preconditioned BiCGSTAB (Sec. 5.4).
+ *
+ * Conventions shared by every entry point:
+ *  - Status: every call returns cpm_status; nothing throws across the ABI.
+ *    A failed call leaves the context usable unless it says otherwise.
+ *  - Pointers named *_dev are DEVICE pointers owned by the caller (never freed
+ *    or retained by the library).  Descriptor structs are host memory and are
+ *    copied during the call.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is enqueued on it; calls that must read results back
+ *    (band build, set-boundary, solves when stats are requested) synchronise it.
+ *  - DOF layout: N = N_S + N_C unknowns; PDE DOFs [0, N_S) are grid nodes of the
+ *    band in canonical order (8^3 bricks by (bz, by, bx), nodes inside a brick by
+ *    (lz, ly, lx)); BC DOFs [N_S, N) follow, ordered by (curve, canonical order of
+ *    their node).  With nrhs > 1, vectors are row-major [N][ld] (right-hand side
+ *    index fastest, nrhs <= ld).
+ *  - Threads: a context may be used from one host thread at a time.
+ */
+#ifndef CPM_H
+#define CPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CPM_OK = 0,
+  CPM_ERR_ARG = 1,           /* bad argument (null pointer, size, unknown kind) */
+  CPM_ERR_OOM = 2,           /* a device or host allocation failed */
+  CPM_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  CPM_ERR_CAPACITY = 4,      /* a fixed-size table (brick hash) overflowed after retries */
+  CPM_ERR_CP_FAILED = 5,     /* a closest-point Newton iteration did not converge */
+  CPM_ERR_OVERLAP = 6,       /* a band node lies within 2 r of two interior boundaries */
+  CPM_ERR_BREAKDOWN = 7,     /* BiCGSTAB broke down after the allowed restarts */
+  CPM_ERR_NOT_CONVERGED = 8, /* the solve reached maxit before the tolerance */
+  CPM_ERR_TIMEOUT = 9,       /* a bounded device or host loop hit its cap */
+  CPM_ERR_STATE = 10         /* call out of order (e.g. apply before set_boundary) */
+} cpm_status;
+
+typedef enum { CPM_SHAPE_CIRCLE = 1, CPM_SHAPE_SPHERE = 2, CPM_SHAPE_TORUS = 3, CPM_SHAPE_BUMPY = 4 } cpm_shape_kind;
+typedef enum { CPM_CURVE_POINT = 1, CPM_CURVE_CIRCLE = 2 } cpm_curve_kind;
+typedef enum { CPM_BC_DIR1 = 1, CPM_BC_DIR2 = 2 } cpm_bc_kind;
+typedef enum { CPM_PREC_FP64 = 0, CPM_PREC_FP32 = 1 } cpm_prec;
+typedef enum { CPM_SOLVE_FP64 = 0, CPM_SOLVE_FP32_IR = 1 } cpm_solve_mode;
+
+/* Manifold S given by its closest-point function (Sec. 3.1, App. A).
+ *  CIRCLE (dim 2): circle of radius R about the origin.
+ *  SPHERE (dim 3): sphere of radius R about the origin.
+ *  TORUS  (dim 3): major radius R, minor radius rt, axis z.
+ *  BUMPY  (dim 3): level set |x| = rho(x/|x|), rho(w) = 1 + amp sum_k a_k
+ *                  exp(-|w - c_k|^2 / width); closest points by the two-stage
+ *                  Newton projection of App. A in FP64.
+ * seed is a point on or near S from which the band search starts (Alg. 1). */
+typedef struct {
+  int kind;
+  int dim;
+  double R;
+  double rt;
+  int K;
+  double amp;
+  double width;
+  const double *a; /* host [K] */
+  const double *c; /* host [3K], unit vectors */
+  double seed[3];
+} cpm_shape_desc;
+
+/* Interior boundary C (Sec. 4).  POINT: p.  CIRCLE: centre p, unit plane normal
+ * nu, radius rad, angle-0 direction ref (unit, in the plane).  nu also orients
+ * the two sides of C: a surface point y is on side sign((y - cp_C) . nu) (for a
+ * point in 2D, nu is the unit tangent of S there; a point in 3D has no sides).
+ * Dirichlet data: n_samples values per side at curve angles 2 pi k / n_samples,
+ * linearly interpolated (periodic); a point takes one value per side. */
+typedef struct {
+  int kind;       /* cpm_curve_kind */
+  int bc;         /* cpm_bc_kind: first- or second-order Dirichlet (Sec. 4.3) */
+  double p[3];
+  double nu[3];
+  double rad;
+  double ref[3];
+  int two_sided;  /* 0: one sample set for both sides; 1: plus-side then minus-side sets */
+  int n_samples;  /* >= 1 */
+} cpm_curve_desc;
+
+typedef struct {
+  double tol;        /* stop when |f - A x|_2 <= tol |f|_2 (per right-hand side) */
+  int maxit;         /* FP64 mode: BiCGSTAB iterations; FP32_IR: total inner iterations */
+  int mode;          /* cpm_solve_mode */
+  double inner_tol;  /* FP32_IR: relative tolerance of each inner FP32 solve (0 -> 1e-4) */
+  int max_refine;    /* FP32_IR: outer refinement steps (0 -> 30) */
+  int check_every;   /* iterations between host convergence checks (0 -> 16) */
+} cpm_solve_opts;
+
+typedef struct {
+  int iterations;    /* BiCGSTAB iterations (FP64) or total inner iterations (FP32_IR) */
+  int refinements;   /* FP32_IR outer steps taken */
+  int restarts;      /* shadow-residual restarts after near breakdown */
+  double relres;     /* final FP64 relative residual |f - A x| / |f| (max over right-hand sides) */
+  int status;        /* cpm_status of this solve */
+} cpm_solve_stats;
+
+typedef struct cpm_ctx cpm_ctx;
+
+/* Builds the band Omega(S) = { grid nodes x = h (i,j,k) : |x - cp_S(x)| <= r }
+ * (Sec. 3.2, Eq. 3 for r; Sec. 5.1 and Alg. 1 for the search), stores cp_S for
+ * every node (FP64) and allocates the context.  r_band <= 0 selects Eq. (3) with
+ * p = 3, q = 1: r = h sqrt(13) in 2D, h sqrt(17) in 3D.  Synchronises `stream`.
+ * Errors: ARG, OOM, CUDA, CAPACITY, CP_FAILED, TIMEOUT.  *out is NULL on error. */
+cpm_status cpm_band_build(const cpm_shape_desc *shape, double h, double r_band, void *stream, cpm_ctx **out);
+
+/* Sizes of the system: N_S PDE DOFs, N_C BC DOFs (0 before cpm_set_boundary),
+ * the band radius used, and the number of 8^3 bricks.  Any output may be NULL. */
+cpm_status cpm_band_info(const cpm_ctx *ctx, int64_t *n_s, int64_t *n_c, double *r_band, int64_t *n_bricks);
+
+/* Copies the band to caller device buffers: grid indices ijk_dev [N_S][3]
+ * (int32) and closest points cp_dev [N_S][3] (FP64), canonical order.  Either
+ * may be NULL.  Asynchronous on `stream`. */
+cpm_status cpm_export_band(const cpm_ctx *ctx, int32_t *ijk_dev, double *cp_dev, void *stream);
+
+/* Sets the interior boundaries (replacing any previous set) and builds the
+ * operator data: Omega(C) and the BC DOFs (Sec. 4.1), the crossing-test flips of
+ * every stencil of rows within 2 r of a curve (Eqs. 10-11, Sec. 4.6), and the
+ * Dirichlet BC rows (Sec. 4.3): u_alpha = g (first order) or
+ * u_alpha + sum wbar u = 2 g with the stencil at cpbar_C = cp_S(2 cp_C - x)
+ * (second order).  n_curves = 0 gives the plain closed-manifold operator.
+ * Synchronises `stream` (the library's internal stream is the one passed to
+ * cpm_band_build).  Errors: ARG, OOM, CUDA, OVERLAP, CP_FAILED. */
+cpm_status cpm_set_boundary(cpm_ctx *ctx, const cpm_curve_desc *curves, int n_curves);
+
+/* Per BC DOF (device outputs, [N_C] each, any may be NULL): PDE twin index,
+ * curve id, cp_C(x_alpha) ([N_C][3]), side of cp_S(x_alpha) (+1/-1/0) and the
+ * curve angle of cp_C(x_alpha) in [0, 2pi) (0 for points).  Asynchronous. */
+cpm_status cpm_export_boundary(const cpm_ctx *ctx, int64_t *twin_dev, int32_t *curve_dev, double *cpc_dev,
+                               int32_t *side_dev, double *param_dev, void *stream);
+
+/* Right-hand side f = [ s ; c_alpha g_alpha ] (Sec. 5.2): s_dev [N_S] (source
+ * extended from cp_S, or NULL for 0) and Dirichlet values g_alpha from either
+ * g_dev [N_C] (one value per BC DOF, for the side opposite cp_S(x_alpha)) or
+ * samples_dev (all curves' sample sets concatenated; per curve n_samples values,
+ * or 2 n_samples when two-sided: plus side first).  c_alpha = 1 for first-order
+ * and 2 for second-order rows.  With nrhs > 1 every array carries nrhs columns
+ * with leading dimension ld.  Asynchronous. */
+cpm_status cpm_rhs(cpm_ctx *ctx, const double *s_dev, const double *g_dev, const double *samples_dev, double *f_dev,
+                   int nrhs, int64_t ld, void *stream);
+
+/* v = A u with A = m I + n [diag L + (L - diag L) E] on PDE rows and the BC rows
+ * (Sec. 5.4's product, fused on the device).  prec selects FP64 (double*) or FP32
+ * (float*) arithmetic and storage for u and v.  u_dev, v_dev: [N] or [N][ld].
+ * Requires cpm_set_boundary (possibly with no curves).  Asynchronous. */
+cpm_status cpm_apply(cpm_ctx *ctx, double m, double n, int prec, const void *u_dev, void *v_dev, int nrhs,
+                     int64_t ld, void *stream);
+
+/* v = A^T u (the transposed product, by a cell-bucketed gather: no atomics). */
+cpm_status cpm_apply_transpose(cpm_ctx *ctx, double m, double n, int prec, const void *u_dev, void *v_dev, int nrhs,
+                               int64_t ld, void *stream);
+
+/* a = E u on the PDE rows (Eq. 1 with the flips of Eq. 10): the side-correct
+ * surface values at cp_S(x_i).  FP64, a_dev [N_S] (or [N_S][ld]).  Asynchronous. */
+cpm_status cpm_extend(cpm_ctx *ctx, const double *u_dev, double *a_dev, int nrhs, int64_t ld, void *stream);
+
+/* Solves A x = f with diagonal-preconditioned BiCGSTAB (Sec. 5.4), preconditioner
+ * diag(m I + n diag L) on PDE rows and 1 on BC rows.  x_dev holds the initial
+ * guess on entry.  FP64 mode iterates in FP64; FP32_IR runs FP32 inner solves
+ * inside FP64 iterative refinement (FP64 residual and update).  All right-hand
+ * sides of a batch iterate together with their own scalars.  The first call with
+ * a given nrhs allocates its workspace inside the context.  Synchronises
+ * `stream`.  stats may be NULL.  Errors: ARG, STATE, OOM, CUDA, BREAKDOWN,
+ * NOT_CONVERGED (x holds the last iterate). */
+cpm_status cpm_solve(cpm_ctx *ctx, double m, double n, const double *f_dev, double *x_dev, int nrhs, int64_t ld,
+                     const cpm_solve_opts *opts, cpm_solve_stats *stats, void *stream);
+
+/* Solves A^T lambda = g (the adjoint system) with the same options. */
+cpm_status cpm_solve_adjoint(cpm_ctx *ctx, double m, double n, const double *g_dev, double *lambda_dev, int nrhs,
+                             int64_t ld, const cpm_solve_opts *opts, cpm_solve_stats *stats, void *stream);
+
+/* Gradient of a loss with respect to the Dirichlet samples given the adjoint
+ * state lambda (A^T lambda = dL/du): dL/dsamples = B^T (c_alpha lambda_alpha),
+ * where B maps samples to g_alpha (periodic linear interpolation per curve and
+ * side).  dLds_dev has the samples layout of cpm_rhs.  Asynchronous. */
+cpm_status cpm_boundary_grad(cpm_ctx *ctx, const double *lambda_dev, double *dLds_dev, int nrhs, int64_t ld,
+                             void *stream);
+
+/* Releases the context and all device memory it owns.  NULL is allowed. */
+void cpm_destroy(cpm_ctx *ctx);
+
+/* Static string naming a status code. */
+const char *cpm_status_str(cpm_status s);
+
+/* Diagnostics: counts of crossing-test flips that found no BC twin (Sec. 4.2;
+ * zero on smooth geometry within interpolation reach) and of special rows. */
+cpm_status cpm_diagnostics(const cpm_ctx *ctx, int64_t *noflip_twin, int64_t *n_special_rows);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPM_H */

@@ -1,0 +1,319 @@
+// apply.cu -- the matrix-free CPM operator on the device.
+//
+// Sec. 5.4 computes v = A u in four passes with stored E and L:
+//   a = E u;  b = (L - diag L) a;  a = diag(L) u;  v = m u + n a + n b.
+// Here E and L are never stored for the bulk of the rows: each PDE row keeps
+// only the packed location of its interpolation stencil's base node and the
+// fractional position t (FP64 and FP32 copies); the cubic Lagrange weights are
+// formed in registers and the separable 4x4x4 gather runs along x-lines whose
+// DOFs are consecutive in the canonical order (a line crossing a brick face is
+// split in two runs).  Rows within 2 r of an interior boundary carry explicit
+// stencils with the crossing-test flips (Eq. 10).  Two kernels per product:
+//   gather : a_i = (E u)_i for PDE rows
+//   combine: v_i = (m + n diagL) u_i + (n/h^2) sum_nbr a_sigma(nbr)   (PDE rows)
+//            v_alpha = sum_beta B_alpha,beta u_beta                   (BC rows)
+// where a neighbour flipped to a BC DOF reads u of that DOF (E rows of BC DOFs
+// are the identity).
+#include "cpm_internal.cuh"
+#include "apply.cuh"
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T line4(const T *u, int64_t ld, int r, int32_t s0, int32_t s1, int split, const T w[4]) {
+  // nodes 0..split-1 are consecutive from s0, nodes split..3 consecutive from s1;
+  // a negative start (a node outside the band, excluded at set-up) reads nothing
+  T acc = T(0);
+#pragma unroll
+  for (int cx = 0; cx < 4; ++cx) {
+    int32_t st = (cx < split) ? s0 : s1;
+    int32_t idx = (cx < split) ? (s0 + cx) : (s1 + (cx - split));
+    if (st >= 0) acc += w[cx] * __ldg(u + (int64_t)idx * ld + r);
+  }
+  return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gather_kernel(ApplyArgs<T> A, const T *__restrict__ u, T *__restrict__ a,
+                                                     int nrhs, int64_t ld) {
+  const int64_t total = A.v.NS * (int64_t)nrhs;
+  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < total;
+       tid += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = tid / nrhs;
+    int r = (int)(tid - i * nrhs);
+    uint32_t rb = __ldg(A.rbase + i);
+    T acc = T(0);
+    if (rb & CPM_SPECIAL_BIT) {
+      int64_t s = __ldg(A.spec_of + i);
+      const int32_t *ec = A.ecol + s * 64;
+      const T *ew = A.ew + s * 64;
+      for (int e = 0; e < 64; ++e) {
+        int32_t c = __ldg(ec + e);
+        if (c >= 0) acc += __ldg(ew + e) * __ldg(u + (int64_t)c * ld + r);
+      }
+    } else {
+      int32_t b = (int32_t)((rb >> 9) & 0x3FFFFFu);
+      int l = (int)(rb & 511u);
+      int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+      T wx[4], wy[4], wz[4];
+      cpm_lagrange4<T>(__ldg(A.t + 3 * i), wx);
+      cpm_lagrange4<T>(__ldg(A.t + 3 * i + 1), wy);
+      const int nz = (A.v.dim == 3) ? 4 : 1;
+      if (A.v.dim == 3) cpm_lagrange4<T>(__ldg(A.t + 3 * i + 2), wz);
+      else { wz[0] = T(1); wz[1] = wz[2] = wz[3] = T(0); }
+      const int split = (lx + 3 < 8) ? 4 : 8 - lx;
+      for (int cz = 0; cz < nz; ++cz) {
+        T pz = T(0);
+#pragma unroll
+        for (int cy = 0; cy < 4; ++cy) {
+          int32_t s0 = cpm_node_index(A.v, b, lx, ly + cy, lz + cz);
+          int32_t s1 = (split < 4) ? cpm_node_index(A.v, b, 8, ly + cy, lz + cz) : 0;
+          pz += wy[cy] * line4<T>(u, ld, r, s0, s1, split, wx);
+        }
+        acc += wz[cz] * pz;
+      }
+    }
+    a[i * ld + r] = acc;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, const T *__restrict__ u,
+                                                      const T *__restrict__ a, T *__restrict__ v, int nrhs,
+                                                      int64_t ld) {
+  const int64_t NS = A.v.NS, N = NS + A.v.NC;
+  const int64_t total = N * (int64_t)nrhs;
+  const T inv_h2 = T(A.v.inv_h * A.v.inv_h);
+  const T diag = m + n * T(-2.0 * A.v.dim * A.v.inv_h * A.v.inv_h);
+  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < total;
+       tid += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = tid / nrhs;
+    int r = (int)(tid - i * nrhs);
+    if (i < NS) {
+      uint32_t rb = __ldg(A.rbase + i);
+      T s = T(0);
+      if (rb & CPM_SPECIAL_BIT) {
+        int64_t sp = __ldg(A.spec_of + i);
+        for (int k = 0; k < 6; ++k) {
+          int32_t c = __ldg(A.fcol + sp * 6 + k);
+          if (c >= 0) s += (c < NS) ? __ldg(a + (int64_t)c * ld + r) : __ldg(u + (int64_t)c * ld + r);
+        }
+      } else {
+        uint32_t rs = __ldg(A.rself + i);
+        int32_t b = (int32_t)(rs >> 9);
+        int l = (int)(rs & 511u);
+        int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+        int32_t j;
+        j = cpm_node_index(A.v, b, lx - 1, ly, lz); if (j >= 0) s += __ldg(a + (int64_t)j * ld + r);
+        j = cpm_node_index(A.v, b, lx + 1, ly, lz); if (j >= 0) s += __ldg(a + (int64_t)j * ld + r);
+        j = cpm_node_index(A.v, b, lx, ly - 1, lz); if (j >= 0) s += __ldg(a + (int64_t)j * ld + r);
+        j = cpm_node_index(A.v, b, lx, ly + 1, lz); if (j >= 0) s += __ldg(a + (int64_t)j * ld + r);
+        if (A.v.dim == 3) {
+          j = cpm_node_index(A.v, b, lx, ly, lz - 1); if (j >= 0) s += __ldg(a + (int64_t)j * ld + r);
+          j = cpm_node_index(A.v, b, lx, ly, lz + 1); if (j >= 0) s += __ldg(a + (int64_t)j * ld + r);
+        }
+      }
+      v[i * ld + r] = diag * __ldg(u + i * ld + r) + (n * inv_h2) * s;
+    } else {
+      int64_t al = i - NS;
+      int cnt = __ldg(A.bc_cnt + al);
+      T s = T(0);
+      for (int e = 0; e < cnt; ++e)
+        s += __ldg(A.bc_val + al * CPM_BC_STRIDE + e) * __ldg(u + (int64_t)__ldg(A.bc_col + al * CPM_BC_STRIDE + e) * ld + r);
+      v[i * ld + r] = s;
+    }
+  }
+}
+
+__global__ void rhs_kernel(BandView v, const CurveDev *curves, const int32_t *bc_curve, const int32_t *side,
+                           const double *param, const double *s, const double *g, const double *samples, double *f,
+                           int nrhs, int64_t ld) {
+  const int64_t N = v.NS + v.NC, total = N * (int64_t)nrhs;
+  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < total;
+       tid += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = tid / nrhs;
+    int r = (int)(tid - i * nrhs);
+    if (i < v.NS) {
+      f[i * ld + r] = s ? s[i * ld + r] : 0.0;
+      continue;
+    }
+    int64_t al = i - v.NS;
+    const CurveDev &cv = curves[bc_curve[al]];
+    double gv = 0.0;
+    if (g) {
+      gv = g[al * ld + r];
+    } else if (samples) {
+      int ns = cv.n_samples;
+      double sp = param[al] / 6.283185307179586476925286766559 * ns;
+      double fl = floor(sp);
+      int i0 = ((int)fl) % ns;
+      if (i0 < 0) i0 += ns;
+      int i1 = (i0 + 1) % ns;
+      double fr = sp - fl;
+      int64_t o = cv.sample_off;
+      double plus = (1.0 - fr) * samples[(o + i0) * ld + r] + fr * samples[(o + i1) * ld + r];
+      if (cv.two_sided) {
+        double minus = (1.0 - fr) * samples[(o + ns + i0) * ld + r] + fr * samples[(o + ns + i1) * ld + r];
+        int sd = side[al];
+        gv = (sd > 0) ? minus : (sd < 0) ? plus : 0.5 * (plus + minus);
+      } else {
+        gv = plus;
+      }
+    }
+    f[i * ld + r] = ((cv.bc == CPM_BC_DIR2) ? 2.0 : 1.0) * gv;
+  }
+}
+
+// dL/dsamples = B^T (c_alpha lambda_alpha): one block per (sample, rhs), a fixed
+// order reduction over the BC DOFs of the sample's curve (deterministic)
+__global__ void boundary_grad_kernel(BandView v, const CurveDev *curves, int ncurves, const int32_t *curve_first,
+                                     const int32_t *side, const double *param, const double *lam, double *out,
+                                     int64_t nsamples_total, int nrhs, int64_t ld) {
+  __shared__ double red[256];
+  for (int64_t q = blockIdx.x; q < nsamples_total * nrhs; q += gridDim.x) {
+    int64_t sidx = q / nrhs;
+    int r = (int)(q - sidx * nrhs);
+    int k = 0;
+    while (k + 1 < ncurves && curves[k + 1].sample_off <= sidx) ++k;
+    const CurveDev &cv = curves[k];
+    int ns = cv.n_samples;
+    int64_t loc = sidx - cv.sample_off;
+    int blockside = (cv.two_sided && loc >= ns) ? -1 : +1;  // plus block first, then minus block
+    int kk = (int)(loc % ns);
+    double acc = 0.0;
+    for (int64_t al = curve_first[k] + threadIdx.x; al < curve_first[k + 1]; al += blockDim.x) {
+      double sp = param[al] / 6.283185307179586476925286766559 * ns;
+      double fl = floor(sp);
+      int i0 = ((int)fl) % ns;
+      if (i0 < 0) i0 += ns;
+      int i1 = (i0 + 1) % ns;
+      double fr = sp - fl;
+      double wblk = 1.0;
+      if (cv.two_sided) {
+        int sd = side[al];
+        // a BC DOF whose cp_S is on the plus side takes the minus-side samples
+        if (sd > 0) wblk = (blockside < 0) ? 1.0 : 0.0;
+        else if (sd < 0) wblk = (blockside > 0) ? 1.0 : 0.0;
+        else wblk = 0.5;
+      }
+      double w = 0.0;
+      if (i0 == kk) w += 1.0 - fr;
+      if (i1 == kk) w += fr;
+      double c = (cv.bc == CPM_BC_DIR2) ? 2.0 : 1.0;
+      acc += wblk * w * c * lam[(v.NS + al) * ld + r];
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[sidx * ld + r] = red[0];
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+template <typename T>
+ApplyArgs<T> cpm_apply_args(const cpm_ctx *c) {
+  ApplyArgs<T> A;
+  A.v = c->view();
+  A.rbase = c->d_rbase;
+  A.rself = c->d_rself;
+  A.spec_of = c->d_spec_of;
+  A.ecol = c->d_spec_ecol;
+  A.fcol = c->d_spec_fcol;
+  A.bc_cnt = c->d_bc_cnt;
+  A.bc_col = c->d_bc_col;
+  if constexpr (sizeof(T) == 8) {
+    A.t = reinterpret_cast<const T *>(c->d_t64);
+    A.ew = reinterpret_cast<const T *>(c->d_spec_ew);
+    A.bc_val = reinterpret_cast<const T *>(c->d_bc_val);
+  } else {
+    A.t = reinterpret_cast<const T *>(c->d_t32);
+    A.ew = reinterpret_cast<const T *>(c->d_spec_ew32);
+    A.bc_val = reinterpret_cast<const T *>(c->d_bc_val32);
+  }
+  return A;
+}
+
+template <typename T>
+void cpm_launch_gather(const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld, cudaStream_t st) {
+  gather_kernel<T><<<cpm_grid(A.v.NS * nrhs, 256), 256, 0, st>>>(A, u, a, nrhs, ld);
+}
+
+template <typename T>
+void cpm_launch_combine(const ApplyArgs<T> &A, T m, T n, const T *u, const T *a, T *v, int nrhs, int64_t ld,
+                        cudaStream_t st) {
+  combine_kernel<T><<<cpm_grid((A.v.NS + A.v.NC) * nrhs, 256), 256, 0, st>>>(A, m, n, u, a, v, nrhs, ld);
+}
+
+template ApplyArgs<double> cpm_apply_args<double>(const cpm_ctx *);
+template ApplyArgs<float> cpm_apply_args<float>(const cpm_ctx *);
+template void cpm_launch_gather<double>(const ApplyArgs<double> &, const double *, double *, int, int64_t,
+                                        cudaStream_t);
+template void cpm_launch_gather<float>(const ApplyArgs<float> &, const float *, float *, int, int64_t, cudaStream_t);
+template void cpm_launch_combine<double>(const ApplyArgs<double> &, double, double, const double *, const double *,
+                                         double *, int, int64_t, cudaStream_t);
+template void cpm_launch_combine<float>(const ApplyArgs<float> &, float, float, const float *, const float *,
+                                        float *, int, int64_t, cudaStream_t);
+
+// v = A u using the context's scratch for a
+template <typename T>
+cpm_status cpm_apply_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld, cudaStream_t st) {
+  cpm_status rc = cpm_ensure(c->a_scratch, sizeof(T) * (size_t)c->NS * (size_t)ld);
+  if (rc) return rc;
+  ApplyArgs<T> A = cpm_apply_args<T>(c);
+  T *a = reinterpret_cast<T *>(c->a_scratch.p);
+  cpm_launch_gather<T>(A, u, a, nrhs, ld, st);
+  cpm_launch_combine<T>(A, (T)m, (T)n, u, a, v, nrhs, ld, st);
+  CPM_CUDA_TRY(cudaGetLastError());
+  return CPM_OK;
+}
+template cpm_status cpm_apply_T<double>(cpm_ctx *, double, double, const double *, double *, int, int64_t,
+                                        cudaStream_t);
+template cpm_status cpm_apply_T<float>(cpm_ctx *, double, double, const float *, float *, int, int64_t,
+                                       cudaStream_t);
+
+cpm_status cpm_internal_extend(cpm_ctx *c, const double *u, double *a, int nrhs, int64_t ld, cudaStream_t st) {
+  ApplyArgs<double> A = cpm_apply_args<double>(c);
+  cpm_launch_gather<double>(A, u, a, nrhs, ld, st);
+  CPM_CUDA_TRY(cudaGetLastError());
+  return CPM_OK;
+}
+
+cpm_status cpm_internal_rhs(cpm_ctx *c, const double *s, const double *g, const double *samples, double *f, int nrhs,
+                            int64_t ld, cudaStream_t st) {
+  int64_t N = c->NS + c->NC;
+  rhs_kernel<<<cpm_grid(N * nrhs, 256), 256, 0, st>>>(c->view(), c->d_curves, c->d_bc_curve, c->d_side, c->d_param, s,
+                                                      g, samples, f, nrhs, ld);
+  CPM_CUDA_TRY(cudaGetLastError());
+  return CPM_OK;
+}
+
+cpm_status cpm_internal_boundary_grad(cpm_ctx *c, const double *lam, double *out, int nrhs, int64_t ld,
+                                      cudaStream_t st) {
+  if (c->nsamples_total == 0) return CPM_OK;
+  // first BC DOF of each curve (BC DOFs are ordered by curve)
+  int n = c->ncurves;
+  std::vector<int32_t> first(n + 1, 0);
+  {
+    std::vector<int32_t> bcc(c->NC);
+    if (c->NC) CPM_CUDA_TRY(cudaMemcpyAsync(bcc.data(), c->d_bc_curve, sizeof(int32_t) * c->NC, cudaMemcpyDeviceToHost, st));
+    CPM_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int k = 0; k <= n; ++k) first[k] = 0;
+    for (int64_t a = 0; a < c->NC; ++a) first[bcc[a] + 1]++;
+    for (int k = 0; k < n; ++k) first[k + 1] += first[k];
+  }
+  int32_t *d_first = nullptr;
+  CPM_CUDA_TRY(cudaMallocAsync(&d_first, sizeof(int32_t) * (n + 1), st));
+  CPM_CUDA_TRY(cudaMemcpyAsync(d_first, first.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st));
+  unsigned grid = (unsigned)std::min<int64_t>(c->nsamples_total * nrhs, 152 * 32);
+  boundary_grad_kernel<<<grid, 256, 0, st>>>(c->view(), c->d_curves, n, d_first, c->d_side, c->d_param, lam, out,
+                                             c->nsamples_total, nrhs, ld);
+  CPM_CUDA_TRY(cudaGetLastError());
+  CPM_CUDA_TRY(cudaFreeAsync(d_first, st));
+  CPM_CUDA_TRY(cudaStreamSynchronize(st));
+  return CPM_OK;
+}

@@ -1,0 +1,44 @@
+// apply.cuh -- launch interface of the operator kernels (see apply.cu).
+#pragma once
+
+#include <algorithm>
+#include <vector>
+
+#include "cpm_internal.cuh"
+
+template <typename T>
+struct ApplyArgs {
+  BandView v;
+  const uint32_t *rbase;
+  const uint32_t *rself;
+  const T *t;
+  const int32_t *spec_of;
+  const int32_t *ecol;
+  const T *ew;
+  const int32_t *fcol;
+  const int32_t *bc_cnt;
+  const int32_t *bc_col;
+  const T *bc_val;
+};
+
+template <typename T>
+ApplyArgs<T> cpm_apply_args(const cpm_ctx *c);
+template <typename T>
+void cpm_launch_gather(const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld, cudaStream_t st);
+template <typename T>
+void cpm_launch_combine(const ApplyArgs<T> &A, T m, T n, const T *u, const T *a, T *v, int nrhs, int64_t ld,
+                        cudaStream_t st);
+template <typename T>
+cpm_status cpm_apply_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld, cudaStream_t st);
+template <typename T>
+cpm_status cpm_apply_transpose_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld,
+                                 cudaStream_t st);
+
+cpm_status cpm_internal_extend(cpm_ctx *c, const double *u, double *a, int nrhs, int64_t ld, cudaStream_t st);
+cpm_status cpm_internal_rhs(cpm_ctx *c, const double *s, const double *g, const double *samples, double *f, int nrhs,
+                            int64_t ld, cudaStream_t st);
+cpm_status cpm_internal_boundary_grad(cpm_ctx *c, const double *lam, double *out, int nrhs, int64_t ld,
+                                      cudaStream_t st);
+cpm_status cpm_internal_band_build(cpm_ctx *c, const cpm_shape_desc *s, double h, double r_band);
+void cpm_internal_free_band(cpm_ctx *c);
+cpm_status cpm_internal_set_boundary(cpm_ctx *c, const cpm_curve_desc *curves, int n);

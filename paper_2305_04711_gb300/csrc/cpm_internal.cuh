@@ -1,0 +1,281 @@
+// cpm_internal.cuh -- device-side data layout and helpers shared by the
+// CUDA translation units of the sm_103a CPM library.
+//
+// Layout in HBM (all owned by one cpm_ctx):
+//   bricks   : nb active 8^3 bricks sorted by (bz, by, bx); per brick the
+//              member mask as 8 x uint64 (one per z layer, bit = ly*8+lx),
+//              the exclusive member count before each layer, the first DOF
+//              index of the brick, and the 27 neighbour bricks (-1 = absent).
+//   nodes    : per PDE DOF its grid index (int3), cp_S (double3), its own
+//              packed location (brick << 9 | local) and the packed location of
+//              its interpolation stencil's base node (bit 31 marks a "special"
+//              row near an interior boundary, whose stencils are stored
+//              explicitly with the crossing-test flips applied).
+//   operator : per PDE row the fractional stencil position t = cp/h - base in
+//              FP64 and FP32; explicit stencils for special rows; Dirichlet BC
+//              rows in a fixed-stride table.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cpm.h"
+
+#define CPM_BRICK 8
+#define CPM_NBR27 27
+#define CPM_SPECIAL_BIT 0x80000000u
+#define CPM_BC_STRIDE 65
+
+// device-side error flags (bit set by kernels, read by the host)
+#define CPM_DEVERR_MISSING_NODE 1u   // an interpolation or FD node was absent
+#define CPM_DEVERR_CP 2u             // a Newton closest point did not converge
+#define CPM_DEVERR_OVERLAP 4u        // a node lies within 2 r of two curves
+#define CPM_DEVERR_HASH 8u           // brick hash table full
+
+struct CurveDev {
+  int kind, bc, two_sided, n_samples;
+  double p[3], nu[3], ref[3], rad;
+  int64_t sample_off;  // offset of this curve's samples in the concatenated layout
+};
+
+struct ShapeDev {
+  int kind, dim, K;
+  double R, rt, amp, width;
+  const double *a;  // device [K]
+  const double *c;  // device [3K]
+};
+
+// read-only view passed by value to kernels
+struct BandView {
+  int dim;
+  double h, inv_h, rband;
+  int64_t nb, NS, NC;
+  const uint64_t *bmask;  // [nb*8]
+  const int32_t *brank;   // [nb*8]
+  const int32_t *bstart;  // [nb+1]
+  const int32_t *bnbr;    // [nb*27]
+};
+
+struct WorkBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+struct SolveWork;
+
+struct cpm_ctx {
+  cudaStream_t stream = nullptr;
+  // geometry
+  ShapeDev shape{};
+  double *d_shape_a = nullptr, *d_shape_c = nullptr;
+  int dim = 3;
+  double h = 0, rband = 0;
+  double shape_seed[3] = {0, 0, 0};
+  // bricks
+  int64_t nb = 0;
+  int64_t *d_bkey = nullptr;    // [nb] packed brick coordinates, canonical order
+  uint64_t *d_bmask = nullptr;  // [nb*8]
+  int32_t *d_brank = nullptr;   // [nb*8]
+  int32_t *d_bstart = nullptr;  // [nb+1]
+  int32_t *d_bnbr = nullptr;    // [nb*27]
+  // nodes
+  int64_t NS = 0;
+  int32_t *d_ijk = nullptr;     // [NS*3]
+  double *d_cp = nullptr;       // [NS*3]
+  uint32_t *d_rself = nullptr;  // [NS] brick << 9 | local
+  uint32_t *d_rbase = nullptr;  // [NS] stencil base location, special bit
+  double *d_t64 = nullptr;      // [NS*3]
+  float *d_t32 = nullptr;       // [NS*3]
+  // boundary
+  bool boundary_set = false;
+  int ncurves = 0;
+  CurveDev *h_curves = nullptr;
+  CurveDev *d_curves = nullptr;
+  int64_t NC = 0;
+  int64_t nsamples_total = 0;
+  int32_t *d_bc_of = nullptr;     // [NS] BC DOF index (>= NS) at this node or -1
+  int8_t *d_near = nullptr;       // [NS] curve whose 2r zone holds the node, or -1
+  int32_t *d_twin = nullptr;      // [NC]
+  int32_t *d_bc_curve = nullptr;  // [NC]
+  double *d_cpc = nullptr;        // [NC*3]
+  int32_t *d_side = nullptr;      // [NC]
+  double *d_param = nullptr;      // [NC]
+  int32_t *d_bc_cnt = nullptr;    // [NC]
+  int32_t *d_bc_col = nullptr;    // [NC*65]
+  double *d_bc_val = nullptr;     // [NC*65]
+  float *d_bc_val32 = nullptr;    // [NC*65]
+  // special rows (rows within 2 r of a curve)
+  int64_t nspec = 0;
+  int32_t *d_spec_row = nullptr;   // [nspec]
+  int32_t *d_spec_of = nullptr;    // [NS] special index or -1
+  int32_t *d_spec_ecol = nullptr;  // [nspec*64]
+  double *d_spec_ew = nullptr;     // [nspec*64]
+  float *d_spec_ew32 = nullptr;    // [nspec*64]
+  int32_t *d_spec_fcol = nullptr;  // [nspec*6]
+  // transposed structure (adjoint)
+  bool transpose_ready = false;
+  int32_t *d_cell_start = nullptr;  // [NS+1] bulk rows bucketed by their base node
+  int32_t *d_cell_rows = nullptr;   // [n bulk rows]
+  int64_t nT = 0;                   // explicit transposed entries (special E/FD rows, BC rows)
+  int32_t *d_T_ptr = nullptr;       // [N+1] CSR over columns
+  int32_t *d_T_row = nullptr;       // [nT] source row
+  int32_t *d_T_kind = nullptr;      // [nT] 0: E entry of special row, 1: FD entry of special row, 2: BC row entry
+  double *d_T_val = nullptr;        // [nT]
+  float *d_T_val32 = nullptr;       // [nT]
+  // scratch
+  WorkBuf a_scratch;                // E u intermediate
+  WorkBuf b_scratch;                // transposed FD intermediate
+  unsigned *d_err = nullptr;        // device error flags
+  unsigned long long *d_counter = nullptr;  // diagnostics counters [4]
+  int64_t noflip_twin = 0;
+  SolveWork *solve = nullptr;
+  SolveWork *solve_adj = nullptr;
+  BandView view() const {
+    BandView v;
+    v.dim = dim; v.h = h; v.inv_h = 1.0 / h; v.rband = rband;
+    v.nb = nb; v.NS = NS; v.NC = NC;
+    v.bmask = d_bmask; v.brank = d_brank; v.bstart = d_bstart; v.bnbr = d_bnbr;
+    return v;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// host status helpers
+#define CPM_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t e_ = (expr);                                \
+    if (e_ != cudaSuccess) return cpm_internal_cuda_err(e_); \
+  } while (0)
+
+cpm_status cpm_internal_cuda_err(cudaError_t e);
+cpm_status cpm_ensure(WorkBuf &b, size_t bytes);
+void cpm_free_boundary(cpm_ctx *c);
+cpm_status cpm_build_transpose(cpm_ctx *c);
+
+static inline unsigned cpm_grid(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 152 * 64) g = 152 * 64;  // grid-stride loops beyond this
+  return (unsigned)g;
+}
+
+// ---------------------------------------------------------------------------
+// device helpers
+
+// integer floor division by 8 and the remainder in [0, 8)
+__host__ __device__ inline int cpm_fdiv8(int v) { return v >> 3; }  // arithmetic shift
+__host__ __device__ inline int cpm_fmod8(int v) { return v & 7; }
+
+// packed brick key: 21 bits per coordinate with offset 2^20
+__host__ __device__ inline int64_t cpm_brick_key(int bx, int by, int bz) {
+  const int64_t o = 1LL << 20;
+  return (((int64_t)bz + o) << 42) | (((int64_t)by + o) << 21) | ((int64_t)bx + o);
+}
+__host__ __device__ inline void cpm_brick_unkey(int64_t k, int &bx, int &by, int &bz) {
+  const int64_t o = 1LL << 20, m = (1LL << 21) - 1;
+  bz = (int)(((k >> 42) & m) - o);
+  by = (int)(((k >> 21) & m) - o);
+  bx = (int)((k & m) - o);
+}
+
+// DOF index of the node at local coordinates (lx, ly, lz) relative to brick b
+// (coordinates may leave [0,8) by up to one brick); -1 if not in the band.
+__device__ __forceinline__ int32_t cpm_node_index(const BandView &v, int32_t b, int lx, int ly, int lz) {
+  int dx = lx >> 3, dy = ly >> 3, dz = lz >> 3;
+  if (dx | dy | dz) {
+    b = __ldg(v.bnbr + (int64_t)b * 27 + 13 + dx + 3 * dy + 9 * dz);
+    if (b < 0) return -1;
+  }
+  lx &= 7; ly &= 7; lz &= 7;
+  int bit = ly * 8 + lx;
+  uint64_t word = __ldg(reinterpret_cast<const unsigned long long *>(v.bmask) + (int64_t)b * 8 + lz);
+  if (!((word >> bit) & 1ull)) return -1;
+  uint64_t below = (bit == 0) ? 0ull : (word & ((1ull << bit) - 1ull));
+  return __ldg(v.bstart + b) + __ldg(v.brank + (int64_t)b * 8 + lz) + __popcll(below);
+}
+
+// --- FP64 geometry with explicit rounding (no FMA contraction) -------------
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rn_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double rn_sqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ double rn_dot3(const double *a, const double *b) {
+  return rn_add(rn_add(rn_mul(a[0], b[0]), rn_mul(a[1], b[1])), rn_mul(a[2], b[2]));
+}
+__device__ __forceinline__ double rn_norm3(const double *a) { return rn_sqrt(rn_dot3(a, a)); }
+
+// grid node coordinates x = h * (i, j, k)
+__device__ __forceinline__ void cpm_node_x(int dim, double h, int i, int j, int k, double x[3]) {
+  x[0] = rn_mul((double)i, h);
+  x[1] = rn_mul((double)j, h);
+  x[2] = (dim == 3) ? rn_mul((double)k, h) : 0.0;
+}
+
+// Newton projection onto the bumpy-sphere level set
+#include "bumpy.cuh"
+
+// cp_S for the analytic shapes (closed forms; medial-axis points take a fixed
+// direction, which keeps the distance exact); returns nonzero on failure.
+__device__ __forceinline__ int cpm_cp_S(const ShapeDev &s, const double *x, double *cp) {
+  if (s.kind == CPM_SHAPE_CIRCLE) {
+    double n = rn_sqrt(rn_add(rn_mul(x[0], x[0]), rn_mul(x[1], x[1])));
+    if (n == 0.0) { cp[0] = s.R; cp[1] = 0.0; cp[2] = 0.0; return 0; }
+    cp[0] = rn_mul(s.R, rn_div(x[0], n)); cp[1] = rn_mul(s.R, rn_div(x[1], n)); cp[2] = 0.0;
+    return 0;
+  }
+  if (s.kind == CPM_SHAPE_SPHERE) {
+    double n = rn_sqrt(rn_add(rn_add(rn_mul(x[0], x[0]), rn_mul(x[1], x[1])), rn_mul(x[2], x[2])));
+    if (n == 0.0) { cp[0] = s.R; cp[1] = 0.0; cp[2] = 0.0; return 0; }
+    cp[0] = rn_mul(s.R, rn_div(x[0], n)); cp[1] = rn_mul(s.R, rn_div(x[1], n)); cp[2] = rn_mul(s.R, rn_div(x[2], n));
+    return 0;
+  }
+  if (s.kind == CPM_SHAPE_TORUS) {
+    double rho = rn_sqrt(rn_add(rn_mul(x[0], x[0]), rn_mul(x[1], x[1])));
+    double ux = 1.0, uy = 0.0;
+    if (rho != 0.0) { ux = rn_div(x[0], rho); uy = rn_div(x[1], rho); }
+    double cx = rn_mul(s.R, ux), cy = rn_mul(s.R, uy);
+    double dx = rn_sub(x[0], cx), dy = rn_sub(x[1], cy), dz = x[2];
+    double m = rn_sqrt(rn_add(rn_add(rn_mul(dx, dx), rn_mul(dy, dy)), rn_mul(dz, dz)));
+    if (m == 0.0) { cp[0] = cx; cp[1] = cy; cp[2] = s.rt; return 0; }
+    cp[0] = rn_add(cx, rn_mul(s.rt, rn_div(dx, m)));
+    cp[1] = rn_add(cy, rn_mul(s.rt, rn_div(dy, m)));
+    cp[2] = rn_mul(s.rt, rn_div(dz, m));
+    return 0;
+  }
+  if (s.kind == CPM_SHAPE_BUMPY) return cpm_cp_bumpy(s, x, cp);
+  return 1;
+}
+
+// cp to an interior boundary: a point, or a circle (centre p, normal nu, radius)
+__device__ __forceinline__ void cpm_cp_C(const CurveDev &cv, const double *x, double *out) {
+  if (cv.kind == CPM_CURVE_POINT) { out[0] = cv.p[0]; out[1] = cv.p[1]; out[2] = cv.p[2]; return; }
+  double w[3] = {rn_sub(x[0], cv.p[0]), rn_sub(x[1], cv.p[1]), rn_sub(x[2], cv.p[2])};
+  double s = rn_dot3(w, cv.nu);
+  double q[3] = {rn_sub(w[0], rn_mul(s, cv.nu[0])), rn_sub(w[1], rn_mul(s, cv.nu[1])), rn_sub(w[2], rn_mul(s, cv.nu[2]))};
+  double nq = rn_norm3(q);
+  if (nq == 0.0) { q[0] = cv.ref[0]; q[1] = cv.ref[1]; q[2] = cv.ref[2]; nq = 1.0; }
+  out[0] = rn_add(cv.p[0], rn_mul(cv.rad, rn_div(q[0], nq)));
+  out[1] = rn_add(cv.p[1], rn_mul(cv.rad, rn_div(q[1], nq)));
+  out[2] = rn_add(cv.p[2], rn_mul(cv.rad, rn_div(q[2], nq)));
+}
+
+// stencil base node floor(y/h) - 1 and t = y/h - base per axis
+__device__ __forceinline__ void cpm_stencil_of(int dim, double h, const double *y, int base[3], double t[3]) {
+  for (int a = 0; a < 3; ++a) {
+    if (a >= dim) { base[a] = 0; t[a] = 0.0; continue; }
+    double s = rn_div(y[a], h);
+    base[a] = (int)floor(s) - 1;
+    t[a] = rn_sub(s, (double)base[a]);
+  }
+}
+
+// 1D cubic Lagrange weights on nodes 0..3 (product form)
+template <typename T>
+__device__ __forceinline__ void cpm_lagrange4(T t, T w[4]) {
+  T a = t, b = t - T(1), c = t - T(2), d = t - T(3);
+  w[0] = -(b * c * d) * T(1.0 / 6.0);
+  w[1] = (a * c * d) * T(0.5);
+  w[2] = -(a * b * d) * T(0.5);
+  w[3] = (a * b * c) * T(1.0 / 6.0);
+}
