@@ -97,20 +97,30 @@ typedef struct {
   int n_samples;  /* >= 1 */
 } cpm_curve_desc;
 
+typedef enum { CPM_NORM_SCALED = 0, CPM_NORM_PLAIN = 1 } cpm_norm;
+
 typedef struct {
-  double tol;        /* stop when |f - A x|_2 <= tol |f|_2 (per right-hand side) */
-  int maxit;         /* FP64 mode: BiCGSTAB iterations; FP32_IR: total inner iterations */
+  double tol;        /* stop when |W (f - A x)|_2 <= tol |W f|_2 per right-hand side, where W is the
+                        Jacobi scaling diag(1/(m + n diag L)) on PDE rows and 1 on BC rows (norm
+                        CPM_NORM_SCALED, the default) or the identity (CPM_NORM_PLAIN) */
+  int maxit;         /* BiCGSTAB iterations (both modes) */
   int mode;          /* cpm_solve_mode */
-  double inner_tol;  /* FP32_IR: relative tolerance of each inner FP32 solve (0 -> 1e-4) */
-  int max_refine;    /* FP32_IR: outer refinement steps (0 -> 30) */
+  double inner_tol;  /* FP32_IR: reliable-update factor delta in (0,1): the FP32 correction is
+                        folded into the FP64 solution and the FP64 residual recomputed once the
+                        FP32 recursive residual has dropped by delta (0 -> 0.1) */
+  int max_refine;    /* FP32_IR: maximum number of FP64 folds (0 -> 200) */
   int check_every;   /* iterations between host convergence checks (0 -> 16) */
+  int norm;          /* cpm_norm.  SCALED iterates on the row-scaled system W A x = W f; PLAIN is
+                        the paper's right-preconditioned form with the unscaled residual */
+  int inner_maxit;   /* FP32_IR: fold at least every this many iterations (0 -> 1000) */
 } cpm_solve_opts;
 
 typedef struct {
-  int iterations;    /* BiCGSTAB iterations (FP64) or total inner iterations (FP32_IR) */
-  int refinements;   /* FP32_IR outer steps taken */
+  int iterations;    /* BiCGSTAB iterations */
+  int refinements;   /* FP32_IR: FP64 folds (refinement steps) taken */
   int restarts;      /* shadow-residual restarts after near breakdown */
-  double relres;     /* final FP64 relative residual |f - A x| / |f| (max over right-hand sides) */
+  double relres;     /* final FP64 relative residual |W (f - A x)| / |W f| in the chosen norm (max over
+                        right-hand sides) */
   int status;        /* cpm_status of this solve */
 } cpm_solve_stats;
 
@@ -175,8 +185,11 @@ cpm_status cpm_extend(cpm_ctx *ctx, const double *u_dev, double *a_dev, int nrhs
 
 /* Solves A x = f with diagonal-preconditioned BiCGSTAB (Sec. 5.4), preconditioner
  * diag(m I + n diag L) on PDE rows and 1 on BC rows.  x_dev holds the initial
- * guess on entry.  FP64 mode iterates in FP64; FP32_IR runs FP32 inner solves
- * inside FP64 iterative refinement (FP64 residual and update).  All right-hand
+ * guess on entry.  FP64 mode iterates in FP64; FP32_IR iterates in FP32 and
+ * refines in FP64: the FP32 correction is folded into the FP64 solution and the
+ * FP64 residual replaces the FP32 recursive one at each reliable update; a
+ * right-hand side whose FP32 phase stops gaining is finished by FP64 BiCGSTAB
+ * from its current iterate, so the result always meets tol in FP64.  All right-hand
  * sides of a batch iterate together with their own scalars.  The first call with
  * a given nrhs allocates its workspace inside the context.  Synchronises
  * `stream`.  stats may be NULL.  Errors: ARG, STATE, OOM, CUDA, BREAKDOWN,
@@ -200,6 +213,17 @@ void cpm_destroy(cpm_ctx *ctx);
 
 /* Static string naming a status code. */
 const char *cpm_status_str(cpm_status s);
+
+/* Instrumentation for benchmarks.  enable = 1 resets the counters and starts
+ * recording a CUDA event pair around every operator product (forward or
+ * transposed, any precision) on the stream it is launched on, and counting
+ * the library's kernel launches; enable = 0 stops recording, synchronises,
+ * and reports the summed device time of the products (ms), their number, the
+ * number of kernel launches since the reset and the number of PDE rows x
+ * right-hand sides processed by the products.  Outputs may be NULL.  Paper:
+ * no counterpart (measurement only). */
+cpm_status cpm_profile(cpm_ctx *ctx, int enable, double *apply_ms, int64_t *apply_calls, int64_t *kernel_launches,
+                       int64_t *row_rhs_processed);
 
 /* Diagnostics: counts of crossing-test flips that found no BC twin (Sec. 4.2;
  * zero on smooth geometry within interpolation reach) and of special rows. */

@@ -17,11 +17,12 @@ STATUS = {0: "CPM_OK", 1: "CPM_ERR_ARG", 2: "CPM_ERR_OOM", 3: "CPM_ERR_CUDA", 4:
           9: "CPM_ERR_TIMEOUT", 10: "CPM_ERR_STATE"}
 PREC_FP64, PREC_FP32 = 0, 1
 SOLVE_FP64, SOLVE_FP32_IR = 0, 1
+NORM_SCALED, NORM_PLAIN = 0, 1
 
 # every entry point that include/cpm.h declares
 EXPORTS = ["cpm_band_build", "cpm_band_info", "cpm_export_band", "cpm_set_boundary", "cpm_export_boundary",
            "cpm_rhs", "cpm_apply", "cpm_apply_transpose", "cpm_extend", "cpm_solve", "cpm_solve_adjoint",
-           "cpm_boundary_grad", "cpm_destroy", "cpm_status_str", "cpm_diagnostics"]
+           "cpm_boundary_grad", "cpm_destroy", "cpm_status_str", "cpm_diagnostics", "cpm_profile"]
 
 
 class ShapeDesc(ctypes.Structure):
@@ -39,7 +40,8 @@ class CurveDesc(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("mode", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int), ("check_every", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("norm", ctypes.c_int), ("inner_maxit", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -77,6 +79,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.cpm_status_str.argtypes = [i]
     L.cpm_status_str.restype = ctypes.c_char_p
     L.cpm_diagnostics.argtypes = [P, pi64, pi64]
+    L.cpm_profile.argtypes = [P, i, ctypes.POINTER(d), pi64, pi64, pi64]
     for name in EXPORTS:
         if name not in ("cpm_destroy", "cpm_status_str"):
             getattr(L, name).restype = ctypes.c_int

@@ -151,6 +151,15 @@ class Band:
         k = self.NC
         return {"twin": twin[:k], "curve": curve[:k], "cpc": cpc[:k], "side": side[:k], "param": param[:k]}
 
+    def profile(self, enable: bool):
+        """Start (True) or stop (False) the library's product timing; stopping
+        returns {apply_ms, applies, launches, row_rhs}."""
+        ms, calls, launches, rr = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        L.check(self._lib.cpm_profile(self._h, 1 if enable else 0, ctypes.byref(ms), ctypes.byref(calls),
+                                      ctypes.byref(launches), ctypes.byref(rr)), "cpm_profile")
+        return None if enable else {"apply_ms": ms.value, "applies": calls.value, "launches": launches.value,
+                                    "row_rhs": rr.value}
+
     def diagnostics(self):
         a, b = ctypes.c_int64(), ctypes.c_int64()
         L.check(self._lib.cpm_diagnostics(self._h, ctypes.byref(a), ctypes.byref(b)), "cpm_diagnostics")
@@ -182,12 +191,13 @@ class Band:
         return a
 
     def solve(self, m: float, n: float, f: torch.Tensor, x0: Optional[torch.Tensor] = None, tol: float = 1e-10,
-              maxit: int = 20000, mode: str = "fp64", inner_tol: float = 1e-4, max_refine: int = 30,
-              check_every: int = 16, adjoint: bool = False, raise_on_error: bool = True):
+              maxit: int = 20000, mode: str = "fp64", inner_tol: float = 0.0, max_refine: int = 0,
+              check_every: int = 16, adjoint: bool = False, raise_on_error: bool = True, norm: str = "scaled",
+              inner_maxit: int = 0):
         nrhs, ld = _layout(f, self.N)
         x = torch.zeros_like(f) if x0 is None else x0.clone()
         o = L.SolveOpts(tol, maxit, L.SOLVE_FP64 if mode == "fp64" else L.SOLVE_FP32_IR, inner_tol, max_refine,
-                        check_every)
+                        check_every, L.NORM_SCALED if norm == "scaled" else L.NORM_PLAIN, inner_maxit)
         st = L.SolveStats()
         fn = self._lib.cpm_solve_adjoint if adjoint else self._lib.cpm_solve
         rc = fn(self._h, float(m), float(n), _ptr(f), _ptr(x), nrhs, ld, ctypes.byref(o), ctypes.byref(st),

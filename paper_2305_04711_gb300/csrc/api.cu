@@ -41,6 +41,7 @@ void cpm_destroy(cpm_ctx *c) {
   cudaFree(c->b_scratch.p);
   cudaFree(c->d_err);
   cudaFree(c->d_counter);
+  for (auto e : c->prof.ev) cudaEventDestroy(e);
   delete c;
 }
 
@@ -194,6 +195,36 @@ cpm_status cpm_boundary_grad(cpm_ctx *c, const double *lam, double *out, int nrh
   if (!c || !lam || !out || bad_batch(nrhs, ld)) return CPM_ERR_ARG;
   if (!c->boundary_set) return CPM_ERR_STATE;
   return cpm_internal_boundary_grad(c, lam, out, nrhs, ld, as_stream(stream));
+}
+
+cpm_status cpm_profile(cpm_ctx *c, int enable, double *apply_ms, int64_t *apply_calls, int64_t *kernel_launches,
+                       int64_t *row_rhs_processed) {
+  if (!c) return CPM_ERR_ARG;
+  Profiler &p = c->prof;
+  if (enable) {
+    p.on = true;
+    p.used = 0;
+    p.applies = 0;
+    p.launches = 0;
+    p.row_rhs = 0;
+    return CPM_OK;
+  }
+  p.on = false;
+  double total = 0.0;
+  if (p.used) {
+    CPM_CUDA_TRY(cudaEventSynchronize(p.ev[p.used - 1]));
+    for (size_t k = 0; k + 1 < p.used; k += 2) {
+      float ms = 0.0f;
+      CPM_CUDA_TRY(cudaEventElapsedTime(&ms, p.ev[k], p.ev[k + 1]));
+      total += ms;
+    }
+  }
+  if (apply_ms) *apply_ms = total;
+  if (apply_calls) *apply_calls = p.applies;
+  if (kernel_launches) *kernel_launches = p.launches;
+  if (row_rhs_processed) *row_rhs_processed = p.row_rhs;
+  p.used = 0;
+  return CPM_OK;
 }
 
 cpm_status cpm_diagnostics(const cpm_ctx *c, int64_t *noflip, int64_t *nspec) {

@@ -19,8 +19,9 @@
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ T line4(const T *u, int64_t ld, int r, int32_t s0, int32_t s1, int split, const T w[4]) {
+template <typename T, bool DIFF>
+__device__ __forceinline__ T line4(const T *u, int64_t ld, int r, int32_t s0, int32_t s1, int split, const T w[4],
+                                   T ui) {
   // nodes 0..split-1 are consecutive from s0, nodes split..3 consecutive from s1;
   // a negative start (a node outside the band, excluded at set-up) reads nothing
   T acc = T(0);
@@ -28,12 +29,19 @@ __device__ __forceinline__ T line4(const T *u, int64_t ld, int r, int32_t s0, in
   for (int cx = 0; cx < 4; ++cx) {
     int32_t st = (cx < split) ? s0 : s1;
     int32_t idx = (cx < split) ? (s0 + cx) : (s1 + (cx - split));
-    if (st >= 0) acc += w[cx] * __ldg(u + (int64_t)idx * ld + r);
+    if (st >= 0) {
+      T val = __ldg(u + (int64_t)idx * ld + r);
+      acc += w[cx] * (DIFF ? (val - ui) : val);
+    }
   }
   return acc;
 }
 
-template <typename T>
+// DIFF: a_i = sum_j w_j (u_j - u_i), the extension's defect, instead of
+// sum_j w_j u_j.  Subtracting neighbouring values first keeps the rounding
+// error relative to the differences (exact when close, Sterbenz), which FP32
+// needs on smooth fields where the Laplacian cancels O(1) values to O(h^2).
+template <typename T, bool DIFF>
 __global__ void __launch_bounds__(256) gather_kernel(ApplyArgs<T> A, const T *__restrict__ u, T *__restrict__ a,
                                                      int nrhs, int64_t ld) {
   const int64_t total = A.v.NS * (int64_t)nrhs;
@@ -43,13 +51,17 @@ __global__ void __launch_bounds__(256) gather_kernel(ApplyArgs<T> A, const T *__
     int r = (int)(tid - i * nrhs);
     uint32_t rb = __ldg(A.rbase + i);
     T acc = T(0);
+    const T ui = DIFF ? __ldg(u + i * ld + r) : T(0);
     if (rb & CPM_SPECIAL_BIT) {
       int64_t s = __ldg(A.spec_of + i);
       const int32_t *ec = A.ecol + s * 64;
       const T *ew = A.ew + s * 64;
       for (int e = 0; e < 64; ++e) {
         int32_t c = __ldg(ec + e);
-        if (c >= 0) acc += __ldg(ew + e) * __ldg(u + (int64_t)c * ld + r);
+        if (c >= 0) {
+          T val = __ldg(u + (int64_t)c * ld + r);
+          acc += __ldg(ew + e) * (DIFF ? (val - ui) : val);
+        }
       }
     } else {
       int32_t b = (int32_t)((rb >> 9) & 0x3FFFFFu);
@@ -68,7 +80,7 @@ __global__ void __launch_bounds__(256) gather_kernel(ApplyArgs<T> A, const T *__
         for (int cy = 0; cy < 4; ++cy) {
           int32_t s0 = cpm_node_index(A.v, b, lx, ly + cy, lz + cz);
           int32_t s1 = (split < 4) ? cpm_node_index(A.v, b, 8, ly + cy, lz + cz) : 0;
-          pz += wy[cy] * line4<T>(u, ld, r, s0, s1, split, wx);
+          pz += wy[cy] * line4<T, DIFF>(u, ld, r, s0, s1, split, wx, ui);
         }
         acc += wz[cz] * pz;
       }
@@ -77,43 +89,63 @@ __global__ void __launch_bounds__(256) gather_kernel(ApplyArgs<T> A, const T *__
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, const T *__restrict__ u,
+// DIFF: a holds the extension defects sum_j w_j (u_j - u_k), and the row is
+// m u_i + (n/h^2) [ sum_present (a_k + (u_k - u_i)) - n_missing u_i ],
+// the same value as m u_i + n [diag(L) u_i + (1/h^2) sum_present (E u)_k].
+template <typename T, bool DIFF>
+__global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, T rowscale, const T *__restrict__ u,
                                                       const T *__restrict__ a, T *__restrict__ v, int nrhs,
                                                       int64_t ld) {
   const int64_t NS = A.v.NS, N = NS + A.v.NC;
   const int64_t total = N * (int64_t)nrhs;
   const T inv_h2 = T(A.v.inv_h * A.v.inv_h);
   const T diag = m + n * T(-2.0 * A.v.dim * A.v.inv_h * A.v.inv_h);
+  const int nfd = 2 * A.v.dim;
   for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < total;
        tid += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = tid / nrhs;
     int r = (int)(tid - i * nrhs);
     if (i < NS) {
       uint32_t rb = __ldg(A.rbase + i);
+      const T ui = __ldg(u + i * ld + r);
       T s = T(0);
+      int present = 0;
       if (rb & CPM_SPECIAL_BIT) {
         int64_t sp = __ldg(A.spec_of + i);
         for (int k = 0; k < 6; ++k) {
           int32_t c = __ldg(A.fcol + sp * 6 + k);
-          if (c >= 0) s += (c < NS) ? __ldg(a + (int64_t)c * ld + r) : __ldg(u + (int64_t)c * ld + r);
+          if (c < 0) continue;
+          ++present;
+          T uc = __ldg(u + (int64_t)c * ld + r);
+          if (DIFF) s += (c < NS) ? (__ldg(a + (int64_t)c * ld + r) + (uc - ui)) : (uc - ui);
+          else s += (c < NS) ? __ldg(a + (int64_t)c * ld + r) : uc;
         }
       } else {
         uint32_t rs = __ldg(A.rself + i);
         int32_t b = (int32_t)(rs >> 9);
         int l = (int)(rs & 511u);
         int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
-        int32_t j;
-        j = cpm_node_index(A.v, b, lx - 1, ly, lz); if (j >= 0) s += __ldg(a + (int64_t)j * ld + r);
-        j = cpm_node_index(A.v, b, lx + 1, ly, lz); if (j >= 0) s += __ldg(a + (int64_t)j * ld + r);
-        j = cpm_node_index(A.v, b, lx, ly - 1, lz); if (j >= 0) s += __ldg(a + (int64_t)j * ld + r);
-        j = cpm_node_index(A.v, b, lx, ly + 1, lz); if (j >= 0) s += __ldg(a + (int64_t)j * ld + r);
-        if (A.v.dim == 3) {
-          j = cpm_node_index(A.v, b, lx, ly, lz - 1); if (j >= 0) s += __ldg(a + (int64_t)j * ld + r);
-          j = cpm_node_index(A.v, b, lx, ly, lz + 1); if (j >= 0) s += __ldg(a + (int64_t)j * ld + r);
+        int32_t nbr[6];
+        nbr[0] = cpm_node_index(A.v, b, lx - 1, ly, lz);
+        nbr[1] = cpm_node_index(A.v, b, lx + 1, ly, lz);
+        nbr[2] = cpm_node_index(A.v, b, lx, ly - 1, lz);
+        nbr[3] = cpm_node_index(A.v, b, lx, ly + 1, lz);
+        nbr[4] = (A.v.dim == 3) ? cpm_node_index(A.v, b, lx, ly, lz - 1) : -1;
+        nbr[5] = (A.v.dim == 3) ? cpm_node_index(A.v, b, lx, ly, lz + 1) : -1;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          int32_t j = nbr[k];
+          if (j < 0) continue;
+          ++present;
+          T aj = __ldg(a + (int64_t)j * ld + r);
+          if (DIFF) s += aj + (__ldg(u + (int64_t)j * ld + r) - ui);
+          else s += aj;
         }
       }
-      v[i * ld + r] = diag * __ldg(u + i * ld + r) + (n * inv_h2) * s;
+      T val;
+      if (DIFF) val = m * ui + (n * inv_h2) * (s - T(nfd - present) * ui);
+      else val = diag * ui + (n * inv_h2) * s;
+      v[i * ld + r] = rowscale * val;
     } else {
       int64_t al = i - NS;
       int cnt = __ldg(A.bc_cnt + al);
@@ -123,6 +155,214 @@ __global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, 
       v[i * ld + r] = s;
     }
   }
+}
+
+// ---- batched products: one warp per row, lanes over right-hand sides --------
+// With many right-hand sides the stencil (indices, weights) is the same for
+// every column, so one warp computes it once per row and each lane carries RPL
+// columns (r = lane * RPL + k): every stencil node is one coalesced load of
+// 32 * RPL contiguous values ([N][ld] layout, ld a multiple of RPL).
+template <typename T, int RPL>
+struct Vec;
+template <> struct Vec<float, 1> { typedef float t; };
+template <> struct Vec<float, 2> { typedef float2 t; };
+template <> struct Vec<float, 4> { typedef float4 t; };
+template <> struct Vec<double, 1> { typedef double t; };
+template <> struct Vec<double, 2> { typedef double2 t; };
+
+template <typename T, int RPL>
+__device__ __forceinline__ void ldv(const T *p, T out[RPL]) {
+  typedef typename Vec<T, RPL>::t V;
+  V v = __ldg(reinterpret_cast<const V *>(p));
+  const T *q = reinterpret_cast<const T *>(&v);
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) out[k] = q[k];
+}
+
+template <typename T, int RPL>
+__device__ __forceinline__ void stv(T *p, const T in[RPL]) {
+  typedef typename Vec<T, RPL>::t V;
+  V v;
+  T *q = reinterpret_cast<T *>(&v);
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) q[k] = in[k];
+  *reinterpret_cast<V *>(p) = v;
+}
+
+// rows: optional list of the rows to process (count entries); NULL: all rows
+template <typename T, bool DIFF, int RPL>
+__global__ void __launch_bounds__(256) gather_batched_kernel(ApplyArgs<T> A, const T *__restrict__ u,
+                                                             T *__restrict__ a, int nrhs, int64_t ld,
+                                                             const int32_t *__restrict__ rows, int64_t count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int col = lane * RPL;
+  const bool on = col < nrhs;
+  const int64_t nrows = rows ? count : A.v.NS;
+  for (int64_t k = warp; k < nrows; k += nwarps) {
+    const int64_t i = rows ? (int64_t)__ldg(rows + k) : k;
+    uint32_t rb = __ldg(A.rbase + i);
+    T acc[RPL], ui[RPL];
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) { acc[k] = T(0); ui[k] = T(0); }
+    if (DIFF && on) ldv<T, RPL>(u + i * ld + col, ui);
+    if (rb & CPM_SPECIAL_BIT) {
+      int64_t s = __ldg(A.spec_of + i);
+      for (int e = 0; e < 64; ++e) {
+        int32_t c = __ldg(A.ecol + s * 64 + e);
+        if (c < 0 || !on) continue;
+        T w = __ldg(A.ew + s * 64 + e), val[RPL];
+        ldv<T, RPL>(u + (int64_t)c * ld + col, val);
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) acc[k] += w * (DIFF ? (val[k] - ui[k]) : val[k]);
+      }
+    } else {
+      int32_t b = (int32_t)((rb >> 9) & 0x3FFFFFu);
+      int l = (int)(rb & 511u);
+      int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+      T wx[4], wy[4], wz[4];
+      cpm_lagrange4<T>(__ldg(A.t + 3 * i), wx);
+      cpm_lagrange4<T>(__ldg(A.t + 3 * i + 1), wy);
+      const int nz = (A.v.dim == 3) ? 4 : 1;
+      if (A.v.dim == 3) cpm_lagrange4<T>(__ldg(A.t + 3 * i + 2), wz);
+      else { wz[0] = T(1); wz[1] = wz[2] = wz[3] = T(0); }
+      const int split = (lx + 3 < 8) ? 4 : 8 - lx;
+      for (int cz = 0; cz < nz; ++cz) {
+        T pz[RPL];
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) pz[k] = T(0);
+#pragma unroll
+        for (int cy = 0; cy < 4; ++cy) {
+          int32_t s0 = cpm_node_index(A.v, b, lx, ly + cy, lz + cz);
+          int32_t s1 = (split < 4) ? cpm_node_index(A.v, b, 8, ly + cy, lz + cz) : 0;
+          T ln[RPL];
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) ln[k] = T(0);
+#pragma unroll
+          for (int cx = 0; cx < 4; ++cx) {
+            int32_t st = (cx < split) ? s0 : s1;
+            int32_t idx = (cx < split) ? (s0 + cx) : (s1 + (cx - split));
+            if (st < 0 || !on) continue;
+            T val[RPL];
+            ldv<T, RPL>(u + (int64_t)idx * ld + col, val);
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) ln[k] += wx[cx] * (DIFF ? (val[k] - ui[k]) : val[k]);
+          }
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) pz[k] += wy[cy] * ln[k];
+        }
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) acc[k] += wz[cz] * pz[k];
+      }
+    }
+    if (on) stv<T, RPL>(a + i * ld + col, acc);
+  }
+}
+
+template <typename T, bool DIFF, int RPL>
+__global__ void __launch_bounds__(256) combine_batched_kernel(ApplyArgs<T> A, T m, T n, T rowscale,
+                                                              const T *__restrict__ u, const T *__restrict__ a,
+                                                              T *__restrict__ v, int nrhs, int64_t ld) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int col = lane * RPL;
+  const bool on = col < nrhs;
+  const int64_t NS = A.v.NS, N = NS + A.v.NC;
+  const T inv_h2 = T(A.v.inv_h * A.v.inv_h);
+  const T diag = m + n * T(-2.0 * A.v.dim * A.v.inv_h * A.v.inv_h);
+  const int nfd = 2 * A.v.dim;
+  for (int64_t i = warp; i < N; i += nwarps) {
+    T out[RPL];
+    if (i < NS) {
+      uint32_t rb = __ldg(A.rbase + i);
+      int32_t nbr[6];
+      bool spec = (rb & CPM_SPECIAL_BIT) != 0;
+      if (spec) {
+        int64_t sp = __ldg(A.spec_of + i);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) nbr[k] = __ldg(A.fcol + sp * 6 + k);
+      } else {
+        uint32_t rs = __ldg(A.rself + i);
+        int32_t b = (int32_t)(rs >> 9);
+        int l = (int)(rs & 511u);
+        int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+        nbr[0] = cpm_node_index(A.v, b, lx - 1, ly, lz);
+        nbr[1] = cpm_node_index(A.v, b, lx + 1, ly, lz);
+        nbr[2] = cpm_node_index(A.v, b, lx, ly - 1, lz);
+        nbr[3] = cpm_node_index(A.v, b, lx, ly + 1, lz);
+        nbr[4] = (A.v.dim == 3) ? cpm_node_index(A.v, b, lx, ly, lz - 1) : -1;
+        nbr[5] = (A.v.dim == 3) ? cpm_node_index(A.v, b, lx, ly, lz + 1) : -1;
+      }
+      if (!on) continue;
+      T ui[RPL], s[RPL];
+      ldv<T, RPL>(u + i * ld + col, ui);
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) s[k] = T(0);
+      int present = 0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        int32_t c = nbr[q];
+        if (c < 0) continue;
+        ++present;
+        T uc[RPL], ac[RPL];
+        if (DIFF || c >= NS) ldv<T, RPL>(u + (int64_t)c * ld + col, uc);
+        if (c < NS) ldv<T, RPL>(a + (int64_t)c * ld + col, ac);
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          if (DIFF) s[k] += (c < NS) ? (ac[k] + (uc[k] - ui[k])) : (uc[k] - ui[k]);
+          else s[k] += (c < NS) ? ac[k] : uc[k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) {
+        T val = DIFF ? (m * ui[k] + (n * inv_h2) * (s[k] - T(nfd - present) * ui[k]))
+                     : (diag * ui[k] + (n * inv_h2) * s[k]);
+        out[k] = rowscale * val;
+      }
+    } else {
+      if (!on) continue;
+      int64_t al = i - NS;
+      int cnt = __ldg(A.bc_cnt + al);
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) out[k] = T(0);
+      for (int e = 0; e < cnt; ++e) {
+        T w = __ldg(A.bc_val + al * CPM_BC_STRIDE + e), val[RPL];
+        ldv<T, RPL>(u + (int64_t)__ldg(A.bc_col + al * CPM_BC_STRIDE + e) * ld + col, val);
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) out[k] += w * val[k];
+      }
+    }
+    stv<T, RPL>(v + i * ld + col, out);
+  }
+}
+
+// batched product: bulk rows through the cell-bucketed gather (cells.cu),
+// rows with explicit stencils one warp each, then the warp-per-row combine
+template <typename T, int RPL>
+static int launch_batched(const cpm_ctx *c, const ApplyArgs<T> &A, T m, T n, T rowscale, const T *u, T *a, T *v,
+                          int nrhs, int64_t ld, cudaStream_t st, bool diff) {
+  const int64_t warps = 152 * 64;  // 8 warps per block, 8 blocks per SM
+  unsigned g = (unsigned)std::min<int64_t>((A.v.NS + A.v.NC + 7) / 8, warps / 8);
+  if (g < 1) g = 1;
+  unsigned gs = (unsigned)std::min<int64_t>((c->nspec + 7) / 8, warps / 8);
+  int launched = 2;
+  cpm_launch_gather_cells<T>(c, A, u, a, nrhs, ld, st, diff);
+  if (diff) {
+    if (c->nspec > 0) {
+      gather_batched_kernel<T, true, RPL><<<gs, 256, 0, st>>>(A, u, a, nrhs, ld, c->d_spec_row, c->nspec);
+      ++launched;
+    }
+    combine_batched_kernel<T, true, RPL><<<g, 256, 0, st>>>(A, m, n, rowscale, u, a, v, nrhs, ld);
+  } else {
+    if (c->nspec > 0) {
+      gather_batched_kernel<T, false, RPL><<<gs, 256, 0, st>>>(A, u, a, nrhs, ld, c->d_spec_row, c->nspec);
+      ++launched;
+    }
+    combine_batched_kernel<T, false, RPL><<<g, 256, 0, st>>>(A, m, n, rowscale, u, a, v, nrhs, ld);
+  }
+  return launched;
 }
 
 __global__ void rhs_kernel(BandView v, const CurveDev *curves, const int32_t *bc_curve, const int32_t *side,
@@ -239,46 +479,98 @@ ApplyArgs<T> cpm_apply_args(const cpm_ctx *c) {
 }
 
 template <typename T>
-void cpm_launch_gather(const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld, cudaStream_t st) {
-  gather_kernel<T><<<cpm_grid(A.v.NS * nrhs, 256), 256, 0, st>>>(A, u, a, nrhs, ld);
+void cpm_launch_gather(const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld, cudaStream_t st, bool diff) {
+  if (diff) gather_kernel<T, true><<<cpm_grid(A.v.NS * nrhs, 256), 256, 0, st>>>(A, u, a, nrhs, ld);
+  else gather_kernel<T, false><<<cpm_grid(A.v.NS * nrhs, 256), 256, 0, st>>>(A, u, a, nrhs, ld);
 }
 
 template <typename T>
-void cpm_launch_combine(const ApplyArgs<T> &A, T m, T n, const T *u, const T *a, T *v, int nrhs, int64_t ld,
-                        cudaStream_t st) {
-  combine_kernel<T><<<cpm_grid((A.v.NS + A.v.NC) * nrhs, 256), 256, 0, st>>>(A, m, n, u, a, v, nrhs, ld);
+void cpm_launch_combine(const ApplyArgs<T> &A, T m, T n, T rowscale, const T *u, const T *a, T *v, int nrhs,
+                        int64_t ld, cudaStream_t st, bool diff) {
+  unsigned g = cpm_grid((A.v.NS + A.v.NC) * nrhs, 256);
+  if (diff) combine_kernel<T, true><<<g, 256, 0, st>>>(A, m, n, rowscale, u, a, v, nrhs, ld);
+  else combine_kernel<T, false><<<g, 256, 0, st>>>(A, m, n, rowscale, u, a, v, nrhs, ld);
 }
 
 template ApplyArgs<double> cpm_apply_args<double>(const cpm_ctx *);
 template ApplyArgs<float> cpm_apply_args<float>(const cpm_ctx *);
 template void cpm_launch_gather<double>(const ApplyArgs<double> &, const double *, double *, int, int64_t,
-                                        cudaStream_t);
-template void cpm_launch_gather<float>(const ApplyArgs<float> &, const float *, float *, int, int64_t, cudaStream_t);
-template void cpm_launch_combine<double>(const ApplyArgs<double> &, double, double, const double *, const double *,
-                                         double *, int, int64_t, cudaStream_t);
-template void cpm_launch_combine<float>(const ApplyArgs<float> &, float, float, const float *, const float *,
-                                        float *, int, int64_t, cudaStream_t);
+                                        cudaStream_t, bool);
+template void cpm_launch_gather<float>(const ApplyArgs<float> &, const float *, float *, int, int64_t, cudaStream_t,
+                                       bool);
+template void cpm_launch_combine<double>(const ApplyArgs<double> &, double, double, double, const double *,
+                                         const double *, double *, int, int64_t, cudaStream_t, bool);
+template void cpm_launch_combine<float>(const ApplyArgs<float> &, float, float, float, const float *, const float *,
+                                        float *, int, int64_t, cudaStream_t, bool);
 
-// v = A u using the context's scratch for a
+// v = R A u using the context's scratch for a; R scales the PDE rows by
+// `rowscale` (1 for the plain product) and leaves the BC rows alone
 template <typename T>
-cpm_status cpm_apply_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld, cudaStream_t st) {
+cpm_status cpm_apply_scaled_T(cpm_ctx *c, double m, double n, double rowscale, const T *u, T *v, int nrhs, int64_t ld,
+                              cudaStream_t st) {
   cpm_status rc = cpm_ensure(c->a_scratch, sizeof(T) * (size_t)c->NS * (size_t)ld);
   if (rc) return rc;
   ApplyArgs<T> A = cpm_apply_args<T>(c);
   T *a = reinterpret_cast<T *>(c->a_scratch.p);
-  cpm_launch_gather<T>(A, u, a, nrhs, ld, st);
-  cpm_launch_combine<T>(A, (T)m, (T)n, u, a, v, nrhs, ld, st);
+  // FP32 uses the difference form (see gather_kernel); FP64 the direct one
+  const bool diff = (sizeof(T) == 4);
+  cpm_prof_begin(c, st);
+  // batched layouts whose columns fill whole warps use the warp-per-row kernels
+  const bool aligned2 = (ld % 2 == 0) && ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v) |
+                                           reinterpret_cast<uintptr_t>(a)) % (2 * sizeof(T)) == 0);
+  int launched = 2;
+  if (nrhs > 32 && nrhs <= 64 && aligned2)
+    launched = launch_batched<T, 2>(c, A, (T)m, (T)n, (T)rowscale, u, a, v, nrhs, ld, st, diff);
+  else if (nrhs >= 16 && nrhs <= 32)
+    launched = launch_batched<T, 1>(c, A, (T)m, (T)n, (T)rowscale, u, a, v, nrhs, ld, st, diff);
+  else {
+    cpm_launch_gather<T>(A, u, a, nrhs, ld, st, diff);
+    cpm_launch_combine<T>(A, (T)m, (T)n, (T)rowscale, u, a, v, nrhs, ld, st, diff);
+  }
+  cpm_prof_end(c, st, c->NS * (int64_t)nrhs);
+  cpm_count_launches(c, launched);
   CPM_CUDA_TRY(cudaGetLastError());
   return CPM_OK;
+}
+template cpm_status cpm_apply_scaled_T<double>(cpm_ctx *, double, double, double, const double *, double *, int,
+                                               int64_t, cudaStream_t);
+template cpm_status cpm_apply_scaled_T<float>(cpm_ctx *, double, double, double, const float *, float *, int, int64_t,
+                                              cudaStream_t);
+
+template <typename T>
+cpm_status cpm_apply_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld, cudaStream_t st) {
+  return cpm_apply_scaled_T<T>(c, m, n, 1.0, u, v, nrhs, ld, st);
 }
 template cpm_status cpm_apply_T<double>(cpm_ctx *, double, double, const double *, double *, int, int64_t,
                                         cudaStream_t);
 template cpm_status cpm_apply_T<float>(cpm_ctx *, double, double, const float *, float *, int, int64_t,
                                        cudaStream_t);
 
+void cpm_prof_begin(cpm_ctx *c, cudaStream_t st) {
+  if (!c->prof.on) return;
+  Profiler &p = c->prof;
+  if (p.used + 2 > p.ev.size()) {
+    for (int k = 0; k < 64; ++k) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) { (void)cudaGetLastError(); p.on = false; return; }
+      p.ev.push_back(e);
+    }
+  }
+  cudaEventRecord(p.ev[p.used], st);
+}
+
+void cpm_prof_end(cpm_ctx *c, cudaStream_t st, int64_t row_rhs) {
+  if (!c->prof.on) return;
+  Profiler &p = c->prof;
+  cudaEventRecord(p.ev[p.used + 1], st);
+  p.used += 2;
+  p.applies += 1;
+  p.row_rhs += row_rhs;
+}
+
 cpm_status cpm_internal_extend(cpm_ctx *c, const double *u, double *a, int nrhs, int64_t ld, cudaStream_t st) {
   ApplyArgs<double> A = cpm_apply_args<double>(c);
-  cpm_launch_gather<double>(A, u, a, nrhs, ld, st);
+  cpm_launch_gather<double>(A, u, a, nrhs, ld, st, false);
   CPM_CUDA_TRY(cudaGetLastError());
   return CPM_OK;
 }

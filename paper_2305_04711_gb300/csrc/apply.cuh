@@ -24,15 +24,25 @@ struct ApplyArgs {
 template <typename T>
 ApplyArgs<T> cpm_apply_args(const cpm_ctx *c);
 template <typename T>
-void cpm_launch_gather(const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld, cudaStream_t st);
+void cpm_launch_gather(const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld, cudaStream_t st, bool diff);
 template <typename T>
-void cpm_launch_combine(const ApplyArgs<T> &A, T m, T n, const T *u, const T *a, T *v, int nrhs, int64_t ld,
-                        cudaStream_t st);
+void cpm_launch_combine(const ApplyArgs<T> &A, T m, T n, T rowscale, const T *u, const T *a, T *v, int nrhs,
+                        int64_t ld, cudaStream_t st, bool diff);
+template <typename T>
+cpm_status cpm_apply_scaled_T(cpm_ctx *c, double m, double n, double rowscale, const T *u, T *v, int nrhs, int64_t ld,
+                              cudaStream_t st);
+template <typename T>
+cpm_status cpm_apply_transpose_scaled_T(cpm_ctx *c, double m, double n, double rowscale, const T *u, T *v, int nrhs,
+                                        int64_t ld, cudaStream_t st);
 template <typename T>
 cpm_status cpm_apply_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld, cudaStream_t st);
 template <typename T>
 cpm_status cpm_apply_transpose_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld,
                                  cudaStream_t st);
+
+template <typename T>
+void cpm_launch_gather_cells(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld,
+                             cudaStream_t st, bool diff);
 
 cpm_status cpm_internal_extend(cpm_ctx *c, const double *u, double *a, int nrhs, int64_t ld, cudaStream_t st);
 cpm_status cpm_internal_rhs(cpm_ctx *c, const double *s, const double *g, const double *samples, double *f, int nrhs,

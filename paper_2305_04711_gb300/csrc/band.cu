@@ -330,8 +330,16 @@ static cpm_status build_once(cpm_ctx *c, int64_t hcap) {
 done:
 #undef TRY
   cudaStreamSynchronize(st);
-  cudaFree(hkeys); cudaFree(hmask); cudaFree(front); cudaFree(next); cudaFree(d_next_n); cudaFree(n_ins);
-  cudaFree(flag); cudaFree(pos); cudaFree(slots); cudaFree(slot_to_sorted); cudaFree(bcount); cudaFree(d_total);
+  if (rc == CPM_OK) {
+    c->d_hkeys = hkeys;  // kept for set-up lookups of far nodes
+    c->d_slot_to_sorted = slot_to_sorted;
+    c->hcap = hcap;
+  } else {
+    cudaFree(hkeys);
+    cudaFree(slot_to_sorted);
+  }
+  cudaFree(hmask); cudaFree(front); cudaFree(next); cudaFree(d_next_n); cudaFree(n_ins);
+  cudaFree(flag); cudaFree(pos); cudaFree(slots); cudaFree(bcount); cudaFree(d_total);
   cudaFree(keys);
   return rc;
 }
@@ -339,7 +347,8 @@ done:
 static void free_band(cpm_ctx *c) {
   cudaFree(c->d_bkey); cudaFree(c->d_bmask); cudaFree(c->d_brank); cudaFree(c->d_bstart); cudaFree(c->d_bnbr);
   cudaFree(c->d_ijk); cudaFree(c->d_cp); cudaFree(c->d_rself); cudaFree(c->d_rbase); cudaFree(c->d_t64);
-  cudaFree(c->d_t32);
+  cudaFree(c->d_t32); cudaFree(c->d_hkeys); cudaFree(c->d_slot_to_sorted);
+  c->d_hkeys = nullptr; c->d_slot_to_sorted = nullptr; c->hcap = 0;
   c->d_bkey = nullptr; c->d_bmask = nullptr; c->d_brank = nullptr; c->d_bstart = nullptr; c->d_bnbr = nullptr;
   c->d_ijk = nullptr; c->d_cp = nullptr; c->d_rself = nullptr; c->d_rbase = nullptr; c->d_t64 = nullptr;
   c->d_t32 = nullptr;

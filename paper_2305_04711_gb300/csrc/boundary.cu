@@ -41,15 +41,15 @@ __device__ __forceinline__ void node_coords(const BView &b, int32_t j, double x[
   cpm_node_x(b.v.dim, b.v.h, b.ijk[3 * j], b.ijk[3 * j + 1], b.ijk[3 * j + 2], x);
 }
 
-// DOF index of grid node (gi, gj, gk), found through the brick of node j (the
-// target must lie within one brick of node j's brick); -1 if absent.
+// DOF index of grid node (gi, gj, gk): through the brick of node j when the
+// node lies within one brick of it, otherwise through the brick hash.
 __device__ __forceinline__ int32_t lookup_near(const BView &b, int32_t j, int gi, int gj, int gk) {
   uint32_t rs = b.rself[j];
   int32_t bj = (int32_t)(rs >> 9);
   int l = (int)(rs & 511u);
   int ox = b.ijk[3 * j] - (l & 7), oy = b.ijk[3 * j + 1] - ((l >> 3) & 7), oz = b.ijk[3 * j + 2] - (l >> 6);
   int lx = gi - ox, ly = gj - oy, lz = gk - oz;
-  if (lx < -8 || lx > 15 || ly < -8 || ly > 15 || lz < -8 || lz > 15) return -1;
+  if (lx < -8 || lx > 15 || ly < -8 || ly > 15 || lz < -8 || lz > 15) return cpm_lookup_global(b.v, gi, gj, gk);
   return cpm_node_index(b.v, bj, lx, ly, lz);
 }
 
@@ -277,7 +277,7 @@ void cpm_free_boundary(cpm_ctx *c) {
   cudaFree(c->d_cpc); cudaFree(c->d_side); cudaFree(c->d_param); cudaFree(c->d_bc_cnt); cudaFree(c->d_bc_col);
   cudaFree(c->d_bc_val); cudaFree(c->d_bc_val32); cudaFree(c->d_spec_row); cudaFree(c->d_spec_of);
   cudaFree(c->d_spec_ecol); cudaFree(c->d_spec_ew); cudaFree(c->d_spec_ew32); cudaFree(c->d_spec_fcol);
-  cudaFree(c->d_cell_start); cudaFree(c->d_cell_rows); cudaFree(c->d_T_ptr); cudaFree(c->d_T_row);
+  cudaFree(c->d_cell_start); cudaFree(c->d_cell_rows); cudaFree(c->d_cell_key); cudaFree(c->d_T_ptr); cudaFree(c->d_T_row);
   cudaFree(c->d_T_kind); cudaFree(c->d_T_val); cudaFree(c->d_T_val32);
   delete[] c->h_curves;
   c->h_curves = nullptr;
@@ -285,7 +285,8 @@ void cpm_free_boundary(cpm_ctx *c) {
   c->d_cpc = nullptr; c->d_side = nullptr; c->d_param = nullptr; c->d_bc_cnt = nullptr; c->d_bc_col = nullptr;
   c->d_bc_val = nullptr; c->d_bc_val32 = nullptr; c->d_spec_row = nullptr; c->d_spec_of = nullptr;
   c->d_spec_ecol = nullptr; c->d_spec_ew = nullptr; c->d_spec_ew32 = nullptr; c->d_spec_fcol = nullptr;
-  c->d_cell_start = nullptr; c->d_cell_rows = nullptr; c->d_T_ptr = nullptr; c->d_T_row = nullptr;
+  c->d_cell_start = nullptr; c->d_cell_rows = nullptr; c->d_cell_key = nullptr; c->d_T_ptr = nullptr;
+  c->ncells = 0; c->nbulk = 0; c->d_T_row = nullptr;
   c->d_T_kind = nullptr; c->d_T_val = nullptr; c->d_T_val32 = nullptr;
   c->transpose_ready = false;
   c->boundary_set = false;
@@ -407,6 +408,11 @@ done:
 #undef TRY
   cudaStreamSynchronize(st);
   cudaFree(inC); cudaFree(flag); cudaFree(pos); cudaFree(cnt); cudaFree(d_total);
+  if (rc != CPM_OK) {
+    cpm_free_boundary(c);
+    return rc;
+  }
+  rc = cpm_build_cells(c);
   if (rc != CPM_OK) {
     cpm_free_boundary(c);
     return rc;

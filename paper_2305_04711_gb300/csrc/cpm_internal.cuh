@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/cpm.h"
 
 #define CPM_BRICK 8
@@ -54,6 +56,10 @@ struct BandView {
   const int32_t *brank;   // [nb*8]
   const int32_t *bstart;  // [nb+1]
   const int32_t *bnbr;    // [nb*27]
+  // brick hash kept after the build for set-up lookups of far nodes
+  const unsigned long long *hkeys;  // [hcap]
+  const int32_t *slot_to_sorted;    // [hcap]
+  int64_t hcap;
 };
 
 struct WorkBuf {
@@ -62,6 +68,16 @@ struct WorkBuf {
 };
 
 struct SolveWork;
+
+// event-pair timing of operator products and a kernel-launch counter
+struct Profiler {
+  bool on = false;
+  int64_t launches = 0;
+  int64_t applies = 0;
+  int64_t row_rhs = 0;
+  std::vector<cudaEvent_t> ev;  // pairs (start, stop), reused
+  size_t used = 0;
+};
 
 struct cpm_ctx {
   cudaStream_t stream = nullptr;
@@ -78,6 +94,9 @@ struct cpm_ctx {
   int32_t *d_brank = nullptr;   // [nb*8]
   int32_t *d_bstart = nullptr;  // [nb+1]
   int32_t *d_bnbr = nullptr;    // [nb*27]
+  unsigned long long *d_hkeys = nullptr;  // brick hash (set-up lookups)
+  int32_t *d_slot_to_sorted = nullptr;
+  int64_t hcap = 0;
   // nodes
   int64_t NS = 0;
   int32_t *d_ijk = nullptr;     // [NS*3]
@@ -114,8 +133,10 @@ struct cpm_ctx {
   int32_t *d_spec_fcol = nullptr;  // [nspec*6]
   // transposed structure (adjoint)
   bool transpose_ready = false;
-  int32_t *d_cell_start = nullptr;  // [NS+1] bulk rows bucketed by their base node
-  int32_t *d_cell_rows = nullptr;   // [n bulk rows]
+  int64_t ncells = 0, nbulk = 0;    // bulk rows bucketed by their stencil base node
+  int32_t *d_cell_start = nullptr;  // [ncells+1]
+  int32_t *d_cell_rows = nullptr;   // [nbulk]
+  uint32_t *d_cell_key = nullptr;   // [ncells] packed base location (brick << 9 | local)
   int64_t nT = 0;                   // explicit transposed entries (special E/FD rows, BC rows)
   int32_t *d_T_ptr = nullptr;       // [N+1] CSR over columns
   int32_t *d_T_row = nullptr;       // [nT] source row
@@ -128,13 +149,17 @@ struct cpm_ctx {
   unsigned *d_err = nullptr;        // device error flags
   unsigned long long *d_counter = nullptr;  // diagnostics counters [4]
   int64_t noflip_twin = 0;
-  SolveWork *solve = nullptr;
+  Profiler prof;
+  SolveWork *solve = nullptr;        // workspace of the solves (per precision form)
   SolveWork *solve_adj = nullptr;
+  SolveWork *solve64 = nullptr;      // FP64 finishing phase of the FP32 form
+  SolveWork *solve_adj64 = nullptr;
   BandView view() const {
     BandView v;
     v.dim = dim; v.h = h; v.inv_h = 1.0 / h; v.rband = rband;
     v.nb = nb; v.NS = NS; v.NC = NC;
     v.bmask = d_bmask; v.brank = d_brank; v.bstart = d_bstart; v.bnbr = d_bnbr;
+    v.hkeys = d_hkeys; v.slot_to_sorted = d_slot_to_sorted; v.hcap = hcap;
     return v;
   }
 };
@@ -148,9 +173,14 @@ struct cpm_ctx {
   } while (0)
 
 cpm_status cpm_internal_cuda_err(cudaError_t e);
+// profiler hooks (no-ops unless enabled)
+inline void cpm_count_launches(cpm_ctx *c, int k) { c->prof.launches += k; }
+void cpm_prof_begin(cpm_ctx *c, cudaStream_t st);
+void cpm_prof_end(cpm_ctx *c, cudaStream_t st, int64_t row_rhs);
 cpm_status cpm_ensure(WorkBuf &b, size_t bytes);
 void cpm_free_boundary(cpm_ctx *c);
 cpm_status cpm_build_transpose(cpm_ctx *c);
+cpm_status cpm_build_cells(cpm_ctx *c);
 
 static inline unsigned cpm_grid(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
@@ -192,6 +222,27 @@ __device__ __forceinline__ int32_t cpm_node_index(const BandView &v, int32_t b, 
   if (!((word >> bit) & 1ull)) return -1;
   uint64_t below = (bit == 0) ? 0ull : (word & ((1ull << bit) - 1ull));
   return __ldg(v.bstart + b) + __ldg(v.brank + (int64_t)b * 8 + lz) + __popcll(below);
+}
+
+// DOF index of grid node (i, j, k) anywhere in the band, through the brick hash
+// (set-up only); -1 if absent.
+__device__ inline int32_t cpm_lookup_global(const BandView &v, int i, int j, int k) {
+  const uint64_t key = (uint64_t)cpm_brick_key(i >> 3, j >> 3, k >> 3);
+  uint64_t x = key;
+  x ^= x >> 33; x *= 0xff51afd7ed558ccdULL; x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ULL; x ^= x >> 33;
+  const uint64_t mask = (uint64_t)v.hcap - 1;
+  uint64_t p = x & mask;
+  for (int64_t probe = 0; probe < v.hcap; ++probe) {
+    unsigned long long kk = v.hkeys[p];
+    if (kk == key) {
+      int32_t b = v.slot_to_sorted[p];
+      if (b < 0) return -1;
+      return cpm_node_index(v, b, i & 7, j & 7, k & 7);
+    }
+    if (kk == 0xFFFFFFFFFFFFFFFFull) return -1;
+    p = (p + 1) & mask;
+  }
+  return -1;
 }
 
 // --- FP64 geometry with explicit rounding (no FMA contraction) -------------

@@ -71,6 +71,23 @@ def test_apply_fp32_and_batched(oracle_mod, torch_mod, name):
     assert np.max(np.abs(V32 - VR)) <= 2e-6 * np.max(np.abs(VR))
 
 
+@pytest.mark.parametrize("name", ["circle_dir2", "sphere_lat_dir2", "torus_mer_dir2"])
+@pytest.mark.parametrize("nrhs", [20, 40, 64])
+def test_apply_warp_per_row_batches(oracle_mod, torch_mod, name, nrhs):
+    """Batched products (one warp per row, lanes over right-hand sides) in FP64
+    and FP32 against the oracle's assembled A, column by column."""
+    torch = torch_mod
+    w = SMALL[name]()
+    band, ref = pair(oracle_mod, w)
+    U = ci.random_vector(ref.N, seed=nrhs, nrhs=nrhs)
+    VR = ref.A(1.0, -0.01) @ U
+    V = band.apply(1.0, -0.01, torch.tensor(U, device="cuda")).cpu().numpy()
+    V32 = band.apply(1.0, -0.01, torch.tensor(U, device="cuda", dtype=torch.float32)).cpu().numpy()
+    for r in range(nrhs):
+        assert rel_inf(V[:, r], VR[:, r]) < 1e-14
+    assert np.max(np.abs(V32 - VR)) <= 2e-6 * np.max(np.abs(VR))
+
+
 @pytest.mark.parametrize("name", ["circle_dir1", "circle_dir2", "sphere_lat_dir2", "torus_mer_dir2",
                                   "sphere_point_dir1"])
 def test_fp64_solve_matches_oracle_direct(oracle_mod, torch_mod, name):
@@ -83,8 +100,10 @@ def test_fp64_solve_matches_oracle_direct(oracle_mod, torch_mod, name):
     f = ref.rhs(s, g)
     fg = band.rhs(s=torch.tensor(s, device="cuda"), g=torch.tensor(g, device="cuda") if ref.NC else None)
     assert rel_inf(fg.cpu().numpy(), f) == 0.0
-    x, st = band.solve(w.m, w.n, fg, tol=1e-13)
+    # tol below the attainable level: the solver stops at its rounding floor
+    x, st = band.solve(w.m, w.n, fg, tol=1e-14, raise_on_error=False)
     xr = ref.solve_direct(w.m, w.n, f)
+    assert st.relres < 1e-12, st
     assert rel_inf(x.cpu().numpy(), xr) < 1e-10, st
 
 
@@ -95,9 +114,9 @@ def test_fp32_refinement_solve_matches_oracle(oracle_mod, torch_mod, name):
     band, ref = pair(oracle_mod, w)
     g = np.where(ref.bc_curve == 0, 0.0, 1.0)
     f = ref.rhs(np.zeros(ref.NS), g)
-    x, st = band.solve(w.m, w.n, torch.tensor(f, device="cuda"), tol=1e-12, mode="fp32_ir")
+    x, st = band.solve(w.m, w.n, torch.tensor(f, device="cuda"), tol=1e-13, mode="fp32_ir", raise_on_error=False)
     xr = ref.solve_direct(w.m, w.n, f)
-    assert st.refinements >= 1
+    assert st.refinements >= 2 and st.relres < 1e-12, st
     assert rel_inf(x.cpu().numpy(), xr) < 1e-9, st
 
 
@@ -110,8 +129,10 @@ def test_batched_solve_each_column_matches(oracle_mod, torch_mod):
     F = np.zeros((ref.N, 6))
     for r in range(6):
         F[:, r] = ref.rhs(np.zeros(ref.NS), G[:, r])
-    x64, st64 = band.solve(0.0, 1.0, torch.tensor(F, device="cuda"), tol=1e-12)
-    x32, st32 = band.solve(0.0, 1.0, torch.tensor(F, device="cuda"), tol=1e-12, mode="fp32_ir")
+    x64, st64 = band.solve(0.0, 1.0, torch.tensor(F, device="cuda"), tol=1e-14, raise_on_error=False)
+    x32, st32 = band.solve(0.0, 1.0, torch.tensor(F, device="cuda"), tol=1e-13, mode="fp32_ir",
+                           raise_on_error=False)
+    assert st64.relres < 1e-12 and st32.relres < 1e-12, (st64, st32)
     lu = __import__("scipy.sparse.linalg", fromlist=["splu"]).splu(ref.A(0.0, 1.0).tocsc())
     for r in range(6):
         xr = lu.solve(F[:, r])
