@@ -157,11 +157,12 @@ __global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, 
   }
 }
 
-// ---- batched products: one warp per row, lanes over right-hand sides --------
-// With many right-hand sides the stencil (indices, weights) is the same for
-// every column, so one warp computes it once per row and each lane carries RPL
-// columns (r = lane * RPL + k): every stencil node is one coalesced load of
-// 32 * RPL contiguous values ([N][ld] layout, ld a multiple of RPL).
+// ---- batched combine: one warp per row, lanes over right-hand sides ---------
+// With many right-hand sides the FD stencil is the same for every column, so
+// one warp reads it once per row and each lane carries RPL columns
+// (r = lane * RPL + k): every neighbour is one coalesced load of 32 * RPL
+// contiguous values ([N][ld] layout, ld a multiple of RPL).  The extension
+// values a = E u come from the cell-bucketed gather (cells.cu).
 template <typename T, int RPL>
 struct Vec;
 template <> struct Vec<float, 1> { typedef float t; };
@@ -189,77 +190,6 @@ __device__ __forceinline__ void stv(T *p, const T in[RPL]) {
   *reinterpret_cast<V *>(p) = v;
 }
 
-// rows: optional list of the rows to process (count entries); NULL: all rows
-template <typename T, bool DIFF, int RPL>
-__global__ void __launch_bounds__(256) gather_batched_kernel(ApplyArgs<T> A, const T *__restrict__ u,
-                                                             T *__restrict__ a, int nrhs, int64_t ld,
-                                                             const int32_t *__restrict__ rows, int64_t count) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int col = lane * RPL;
-  const bool on = col < nrhs;
-  const int64_t nrows = rows ? count : A.v.NS;
-  for (int64_t k = warp; k < nrows; k += nwarps) {
-    const int64_t i = rows ? (int64_t)__ldg(rows + k) : k;
-    uint32_t rb = __ldg(A.rbase + i);
-    T acc[RPL], ui[RPL];
-#pragma unroll
-    for (int k = 0; k < RPL; ++k) { acc[k] = T(0); ui[k] = T(0); }
-    if (DIFF && on) ldv<T, RPL>(u + i * ld + col, ui);
-    if (rb & CPM_SPECIAL_BIT) {
-      int64_t s = __ldg(A.spec_of + i);
-      for (int e = 0; e < 64; ++e) {
-        int32_t c = __ldg(A.ecol + s * 64 + e);
-        if (c < 0 || !on) continue;
-        T w = __ldg(A.ew + s * 64 + e), val[RPL];
-        ldv<T, RPL>(u + (int64_t)c * ld + col, val);
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) acc[k] += w * (DIFF ? (val[k] - ui[k]) : val[k]);
-      }
-    } else {
-      int32_t b = (int32_t)((rb >> 9) & 0x3FFFFFu);
-      int l = (int)(rb & 511u);
-      int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
-      T wx[4], wy[4], wz[4];
-      cpm_lagrange4<T>(__ldg(A.t + 3 * i), wx);
-      cpm_lagrange4<T>(__ldg(A.t + 3 * i + 1), wy);
-      const int nz = (A.v.dim == 3) ? 4 : 1;
-      if (A.v.dim == 3) cpm_lagrange4<T>(__ldg(A.t + 3 * i + 2), wz);
-      else { wz[0] = T(1); wz[1] = wz[2] = wz[3] = T(0); }
-      const int split = (lx + 3 < 8) ? 4 : 8 - lx;
-      for (int cz = 0; cz < nz; ++cz) {
-        T pz[RPL];
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) pz[k] = T(0);
-#pragma unroll
-        for (int cy = 0; cy < 4; ++cy) {
-          int32_t s0 = cpm_node_index(A.v, b, lx, ly + cy, lz + cz);
-          int32_t s1 = (split < 4) ? cpm_node_index(A.v, b, 8, ly + cy, lz + cz) : 0;
-          T ln[RPL];
-#pragma unroll
-          for (int k = 0; k < RPL; ++k) ln[k] = T(0);
-#pragma unroll
-          for (int cx = 0; cx < 4; ++cx) {
-            int32_t st = (cx < split) ? s0 : s1;
-            int32_t idx = (cx < split) ? (s0 + cx) : (s1 + (cx - split));
-            if (st < 0 || !on) continue;
-            T val[RPL];
-            ldv<T, RPL>(u + (int64_t)idx * ld + col, val);
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) ln[k] += wx[cx] * (DIFF ? (val[k] - ui[k]) : val[k]);
-          }
-#pragma unroll
-          for (int k = 0; k < RPL; ++k) pz[k] += wy[cy] * ln[k];
-        }
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) acc[k] += wz[cz] * pz[k];
-      }
-    }
-    if (on) stv<T, RPL>(a + i * ld + col, acc);
-  }
-}
-
 template <typename T, bool DIFF, int RPL>
 __global__ void __launch_bounds__(256) combine_batched_kernel(ApplyArgs<T> A, T m, T n, T rowscale,
                                                               const T *__restrict__ u, const T *__restrict__ a,
@@ -276,10 +206,12 @@ __global__ void __launch_bounds__(256) combine_batched_kernel(ApplyArgs<T> A, T 
   for (int64_t i = warp; i < N; i += nwarps) {
     T out[RPL];
     if (i < NS) {
-      uint32_t rb = __ldg(A.rbase + i);
       int32_t nbr[6];
-      bool spec = (rb & CPM_SPECIAL_BIT) != 0;
-      if (spec) {
+      if (A.nbr8) {
+        const int4 n0 = __ldg(reinterpret_cast<const int4 *>(A.nbr8 + i * 8));
+        const int2 n1 = __ldg(reinterpret_cast<const int2 *>(A.nbr8 + i * 8 + 4));
+        nbr[0] = n0.x; nbr[1] = n0.y; nbr[2] = n0.z; nbr[3] = n0.w; nbr[4] = n1.x; nbr[5] = n1.y;
+      } else if (__ldg(A.rbase + i) & CPM_SPECIAL_BIT) {
         int64_t sp = __ldg(A.spec_of + i);
 #pragma unroll
         for (int k = 0; k < 6; ++k) nbr[k] = __ldg(A.fcol + sp * 6 + k);
@@ -338,30 +270,17 @@ __global__ void __launch_bounds__(256) combine_batched_kernel(ApplyArgs<T> A, T 
   }
 }
 
-// batched product: bulk rows through the cell-bucketed gather (cells.cu),
-// rows with explicit stencils one warp each, then the warp-per-row combine
+// batched product: E u for all PDE rows through the cell-bucketed gather
+// (cells.cu), then the warp-per-row combine
 template <typename T, int RPL>
 static int launch_batched(const cpm_ctx *c, const ApplyArgs<T> &A, T m, T n, T rowscale, const T *u, T *a, T *v,
                           int nrhs, int64_t ld, cudaStream_t st, bool diff) {
   const int64_t warps = 152 * 64;  // 8 warps per block, 8 blocks per SM
   unsigned g = (unsigned)std::min<int64_t>((A.v.NS + A.v.NC + 7) / 8, warps / 8);
   if (g < 1) g = 1;
-  unsigned gs = (unsigned)std::min<int64_t>((c->nspec + 7) / 8, warps / 8);
-  int launched = 2;
-  cpm_launch_gather_cells<T>(c, A, u, a, nrhs, ld, st, diff);
-  if (diff) {
-    if (c->nspec > 0) {
-      gather_batched_kernel<T, true, RPL><<<gs, 256, 0, st>>>(A, u, a, nrhs, ld, c->d_spec_row, c->nspec);
-      ++launched;
-    }
-    combine_batched_kernel<T, true, RPL><<<g, 256, 0, st>>>(A, m, n, rowscale, u, a, v, nrhs, ld);
-  } else {
-    if (c->nspec > 0) {
-      gather_batched_kernel<T, false, RPL><<<gs, 256, 0, st>>>(A, u, a, nrhs, ld, c->d_spec_row, c->nspec);
-      ++launched;
-    }
-    combine_batched_kernel<T, false, RPL><<<g, 256, 0, st>>>(A, m, n, rowscale, u, a, v, nrhs, ld);
-  }
+  int launched = 1 + cpm_launch_gather_cells<T>(c, A, u, a, nrhs, ld, st, diff, RPL);
+  if (diff) combine_batched_kernel<T, true, RPL><<<g, 256, 0, st>>>(A, m, n, rowscale, u, a, v, nrhs, ld);
+  else combine_batched_kernel<T, false, RPL><<<g, 256, 0, st>>>(A, m, n, rowscale, u, a, v, nrhs, ld);
   return launched;
 }
 
@@ -464,6 +383,7 @@ ApplyArgs<T> cpm_apply_args(const cpm_ctx *c) {
   A.spec_of = c->d_spec_of;
   A.ecol = c->d_spec_ecol;
   A.fcol = c->d_spec_fcol;
+  A.nbr8 = c->d_nbr8;
   A.bc_cnt = c->d_bc_cnt;
   A.bc_col = c->d_bc_col;
   if constexpr (sizeof(T) == 8) {
@@ -519,7 +439,8 @@ cpm_status cpm_apply_scaled_T(cpm_ctx *c, double m, double n, double rowscale, c
   const bool aligned2 = (ld % 2 == 0) && ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v) |
                                            reinterpret_cast<uintptr_t>(a)) % (2 * sizeof(T)) == 0);
   int launched = 2;
-  if (nrhs > 32 && nrhs <= 64 && aligned2)
+  // two adjacent columns per lane need an even column count and 2-element alignment
+  if (nrhs > 32 && nrhs <= 64 && nrhs % 2 == 0 && aligned2)
     launched = launch_batched<T, 2>(c, A, (T)m, (T)n, (T)rowscale, u, a, v, nrhs, ld, st, diff);
   else if (nrhs >= 16 && nrhs <= 32)
     launched = launch_batched<T, 1>(c, A, (T)m, (T)n, (T)rowscale, u, a, v, nrhs, ld, st, diff);

@@ -16,6 +16,7 @@ struct ApplyArgs {
   const int32_t *ecol;
   const T *ew;
   const int32_t *fcol;
+  const int32_t *nbr8;  // [NS][8] FD neighbour columns (NULL: computed per row)
   const int32_t *bc_cnt;
   const int32_t *bc_col;
   const T *bc_val;
@@ -40,9 +41,11 @@ template <typename T>
 cpm_status cpm_apply_transpose_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld,
                                  cudaStream_t st);
 
+// cell-bucketed E u for all PDE rows plus the flipped-entry correction of the
+// rows near curves (batched layouts); returns the number of kernels launched
 template <typename T>
-void cpm_launch_gather_cells(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld,
-                             cudaStream_t st, bool diff);
+int cpm_launch_gather_cells(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld,
+                            cudaStream_t st, bool diff, int rpl);
 
 cpm_status cpm_internal_extend(cpm_ctx *c, const double *u, double *a, int nrhs, int64_t ld, cudaStream_t st);
 cpm_status cpm_internal_rhs(cpm_ctx *c, const double *s, const double *g, const double *samples, double *f, int nrhs,

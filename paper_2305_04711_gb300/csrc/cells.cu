@@ -1,17 +1,21 @@
-// cells.cu -- rows bucketed by the base node ("cell") of their interpolation
-// stencil, and the cell-bucketed batched gather.
+// cells.cu -- PDE rows bucketed by the base node ("cell") of their
+// interpolation stencil, and the batched products built on the buckets.
 //
 // All rows whose closest points fall in the same grid cell share the same
 // 4x4x4 stencil nodes (Eq. 1); only their weights differ.  On a narrow band
-// about 2 r / h ~ 8 rows share each cell.  With many right-hand sides the gather
-// is bound by moving node values (64 nodes x nrhs per row), so one warp takes a
-// whole cell: it loads the 64 nodes once and applies the separable weights of
-// up to 8 of the cell's rows at a time (weights staged in shared memory).
+// several rows (about 2 r / h divided by the number of cells the surface
+// crosses per normal line, ~5 in 3D) share each cell.  With many right-hand
+// sides the extension E u is bound by moving node values, so one warp takes a
+// whole cell: it holds the cell's node values for its columns in registers and
+// applies the separable weights of every row of the cell to them.
+//
+// Rows near an interior boundary use the same cell gather; the entries their
+// crossing test flipped (node j replaced by its BC twin, Sec. 4) are applied
+// afterwards as a sparse correction w (u_twin - u_j) from a list built here.
 //
 // The buckets are built by a counting sort over the dense (brick, local) key
-// space, with each bucket then ordered by row index, so the result does not
-// depend on the scheduling of the atomics.  Only bulk rows are bucketed; rows
-// with explicit (flipped) stencils near interior boundaries keep their own path.
+// space, with each bucket then ordered by row index, so the layout does not
+// depend on the scheduling of the atomics.
 #include <algorithm>
 
 #include "apply.cuh"
@@ -21,18 +25,13 @@
 namespace {
 
 __global__ void cell_count_kernel(const uint32_t *rbase, int64_t NS, int32_t *count) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < NS; i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t rb = rbase[i];
-    if (rb & CPM_SPECIAL_BIT) continue;
-    atomicAdd(count + rb, 1);
-  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < NS; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(count + (rbase[i] & ~CPM_SPECIAL_BIT), 1);
 }
 
 __global__ void cell_scatter_kernel(const uint32_t *rbase, int64_t NS, int32_t *cursor, int32_t *rows) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < NS; i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t rb = rbase[i];
-    if (rb & CPM_SPECIAL_BIT) continue;
-    int32_t p = atomicAdd(cursor + rb, 1);
+    int32_t p = atomicAdd(cursor + (rbase[i] & ~CPM_SPECIAL_BIT), 1);
     rows[p] = (int32_t)i;
   }
 }
@@ -60,135 +59,231 @@ __global__ void flag_nonzero_kernel(const int32_t *count, int64_t n, int32_t *fl
     flag[k] = count[k] != 0;
 }
 
-constexpr int CHUNK = 8;   // rows of a cell processed together
+__global__ void set_i32_kernel(int32_t *p, int32_t v) { *p = v; }
+
+// FD neighbour columns of every PDE row (x-, x+, y-, y+, z-, z+; -1 where
+// absent; the flipped columns for rows near interior boundaries), padded to 8
+__global__ void nbr8_kernel(BandView v, const uint32_t *rself, const uint32_t *rbase, const int32_t *spec_of,
+                            const int32_t *fcol, int32_t *nbr8) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.NS; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t o[8];
+    if (rbase[i] & CPM_SPECIAL_BIT) {
+      const int64_t sp = spec_of[i];
+      for (int k = 0; k < 6; ++k) o[k] = fcol[sp * 6 + k];
+    } else {
+      const uint32_t rs = rself[i];
+      const int32_t b = (int32_t)(rs >> 9);
+      const int l = (int)(rs & 511u);
+      const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+      o[0] = cpm_node_index(v, b, lx - 1, ly, lz);
+      o[1] = cpm_node_index(v, b, lx + 1, ly, lz);
+      o[2] = cpm_node_index(v, b, lx, ly - 1, lz);
+      o[3] = cpm_node_index(v, b, lx, ly + 1, lz);
+      o[4] = (v.dim == 3) ? cpm_node_index(v, b, lx, ly, lz - 1) : -1;
+      o[5] = (v.dim == 3) ? cpm_node_index(v, b, lx, ly, lz + 1) : -1;
+    }
+    o[6] = o[7] = -1;
+    int4 *dst = reinterpret_cast<int4 *>(nbr8 + i * 8);
+    dst[0] = make_int4(o[0], o[1], o[2], o[3]);
+    dst[1] = make_int4(o[4], o[5], o[6], o[7]);
+  }
+}
+
+// node of stencil entry e (x fastest) of the row with packed base rb
+__device__ __forceinline__ int32_t entry_node(const BandView &v, uint32_t rb, int e) {
+  const int32_t b = (int32_t)((rb & ~CPM_SPECIAL_BIT) >> 9);
+  const int l = (int)(rb & 511u);
+  return cpm_node_index(v, b, (l & 7) + (e & 3), ((l >> 3) & 7) + ((e >> 2) & 3), (l >> 6) + (e >> 4));
+}
+
+// number of flipped interpolation entries of each special row
+__global__ void corr_count_kernel(BandView v, const int32_t *spec_row, int64_t nspec, const uint32_t *rbase,
+                                  const int32_t *ecol, int32_t *cnt) {
+  const int ne = (v.dim == 3) ? 64 : 16;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nspec; s += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t rb = rbase[spec_row[s]];
+    int n = 0;
+    for (int e = 0; e < ne; ++e) n += (ecol[s * 64 + e] != entry_node(v, rb, e));
+    cnt[s] = n;
+  }
+}
+
+__global__ void corr_fill_kernel(BandView v, const int32_t *spec_row, int64_t nspec, const uint32_t *rbase,
+                                 const int32_t *ecol, const double *ew, const int32_t *cnt, const int32_t *offs,
+                                 const int32_t *rowpos, int32_t *corr_row, int32_t *corr_start, int32_t *node,
+                                 int32_t *col, double *w64, float *w32) {
+  const int ne = (v.dim == 3) ? 64 : 16;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nspec; s += (int64_t)gridDim.x * blockDim.x) {
+    if (cnt[s] == 0) continue;
+    const int32_t i = spec_row[s];
+    const uint32_t rb = rbase[i];
+    corr_row[rowpos[s]] = i;
+    corr_start[rowpos[s]] = offs[s];
+    int32_t o = offs[s];
+    for (int e = 0; e < ne; ++e) {
+      const int32_t j = entry_node(v, rb, e), ce = ecol[s * 64 + e];
+      if (ce == j) continue;
+      node[o] = j;
+      col[o] = ce;
+      w64[o] = ew[s * 64 + e];
+      w32[o] = (float)ew[s * 64 + e];
+      ++o;
+    }
+  }
+}
+
+constexpr int CHUNK = 8;   // rows of a cell whose weights are staged together
 constexpr int WARPS = 8;   // warps per block
 
-template <typename T, int RPL>
+template <typename T, int R>
 struct VecT;
 template <> struct VecT<float, 1> { typedef float t; };
 template <> struct VecT<float, 2> { typedef float2 t; };
 template <> struct VecT<double, 1> { typedef double t; };
 template <> struct VecT<double, 2> { typedef double2 t; };
 
-template <typename T, int RPL>
-__device__ __forceinline__ void ld(const T *p, T out[RPL]) {
-  typedef typename VecT<T, RPL>::t V;
-  V v = __ldg(reinterpret_cast<const V *>(p));
-  const T *q = reinterpret_cast<const T *>(&v);
+template <typename T, int R>
+__device__ __forceinline__ void vld(const T *p, T out[R]) {
+  typedef typename VecT<T, R>::t V;
+  const V x = __ldg(reinterpret_cast<const V *>(p));
+  const T *q = reinterpret_cast<const T *>(&x);
 #pragma unroll
-  for (int k = 0; k < RPL; ++k) out[k] = q[k];
+  for (int k = 0; k < R; ++k) out[k] = q[k];
 }
 
-template <typename T, int RPL>
-__device__ __forceinline__ void st(T *p, const T in[RPL]) {
-  typedef typename VecT<T, RPL>::t V;
-  V v;
-  T *q = reinterpret_cast<T *>(&v);
+template <typename T, int R>
+__device__ __forceinline__ void vst(T *p, const T in[R]) {
+  typedef typename VecT<T, R>::t V;
+  V x;
+  T *q = reinterpret_cast<T *>(&x);
 #pragma unroll
-  for (int k = 0; k < RPL; ++k) q[k] = in[k];
-  *reinterpret_cast<V *>(p) = v;
+  for (int k = 0; k < R; ++k) q[k] = in[k];
+  *reinterpret_cast<V *>(p) = x;
 }
 
-// One warp per cell.  DIFF (the FP32 form): the node values enter as
-// differences to the cell's base-node value u_c, and each row adds u_c - u_i:
-// sum_n w_n (u_n - u_i) = sum_n w_n (u_n - u_c) + (u_c - u_i) since sum_n w_n = 1,
-// which keeps FP32 rounding relative to local differences.
-template <typename T, bool DIFF, int RPL>
-__global__ void __launch_bounds__(WARPS * 32) gather_cells_kernel(ApplyArgs<T> A, const int32_t *__restrict__ cstart,
-                                                                  const uint32_t *__restrict__ ckey,
-                                                                  const int32_t *__restrict__ crows, int64_t ncells,
-                                                                  const T *__restrict__ u, T *__restrict__ a, int nrhs,
-                                                                  int64_t ld_) {
-  __shared__ T s_wx[WARPS][CHUNK][4];
-  __shared__ T s_wyz[WARPS][CHUNK][16];
+// One warp per cell; each lane takes R adjacent columns (32 R per group).  For
+// a group the lane loads the cell's node values (NX x positions per pass, XH
+// passes) into registers and applies each row of the cell: the y-z weights
+// along each x position (P[cx] = sum_{cy,cz} w_y w_z u), then the x weights.
+// Partial sums of the passes wait in shared memory.
+//
+// DIFF (the FP32 form): the node values enter as differences to the cell's
+// base-node value u_c and each row adds u_c - u_i, which equals
+// sum_n w_n (u_n - u_i) since sum_n w_n = 1; rounding then stays relative to
+// local differences.
+template <typename T, bool DIFF, int DIM, int XH, int R>
+__global__ void __launch_bounds__(WARPS * 32, 2)
+    gather_cells_kernel(ApplyArgs<T> A, const int32_t *__restrict__ cstart, const uint32_t *__restrict__ ckey,
+                        const int32_t *__restrict__ crows, int64_t ncells, const T *__restrict__ u,
+                        T *__restrict__ a, int nrhs, int64_t ld_) {
+  constexpr int NZ = (DIM == 3) ? 4 : 1;
+  constexpr int NL = 4 * NZ;  // stencil lines along x
+  constexpr int NN = 4 * NL;  // stencil nodes
+  constexpr int NX = 4 / XH;  // x positions per pass
+  typedef typename VecT<T, R>::t V;
+  __shared__ __align__(16) T s_wyz[WARPS][CHUNK][NL];
+  __shared__ __align__(16) T s_wx[WARPS][CHUNK][4];
   __shared__ int32_t s_row[WARPS][CHUNK];
-  __shared__ int32_t s_line[WARPS][16][2];
+  __shared__ __align__(16) int32_t s_idx[WARPS][NN];
+  __shared__ V s_acc[(XH > 1) ? WARPS : 1][CHUNK][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int col = lane * RPL;
-  const bool on = col < nrhs;
-  const int nz = (A.v.dim == 3) ? 4 : 1;
-  const int nlines = 4 * nz;
+  const int ngroups = (nrhs + 32 * R - 1) / (32 * R);
   for (int64_t cid = warp; cid < ncells; cid += nwarps) {
     const uint32_t key = __ldg(ckey + cid);
-    const int32_t b = (int32_t)(key >> 9);
-    const int l = (int)(key & 511u);
-    const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
-    const int split = (lx + 3 < 8) ? 4 : 8 - lx;
-    if (lane < nlines) {
-      int cy = lane & 3, cz = lane >> 2;
-      s_line[wib][lane][0] = cpm_node_index(A.v, b, lx, ly + cy, lz + cz);
-      s_line[wib][lane][1] = (split < 4) ? cpm_node_index(A.v, b, 8, ly + cy, lz + cz) : 0;
-    }
+    for (int e = lane; e < NN; e += 32) s_idx[wib][e] = entry_node(A.v, key, e);
     __syncwarp();
-    T uc[RPL];
-#pragma unroll
-    for (int k = 0; k < RPL; ++k) uc[k] = T(0);
-    if (DIFF && on && s_line[wib][0][0] >= 0) ld<T, RPL>(u + (int64_t)s_line[wib][0][0] * ld_ + col, uc);
+    const int32_t base = s_idx[wib][0];
     const int32_t r0 = __ldg(cstart + cid), r1 = __ldg(cstart + cid + 1);
     for (int32_t cs = r0; cs < r1; cs += CHUNK) {
       const int k = min(CHUNK, r1 - cs);
       if (lane < k) {
-        int32_t row = __ldg(crows + cs + lane);
+        const int32_t row = __ldg(crows + cs + lane);
         s_row[wib][lane] = row;
         T wx[4], wy[4], wz[4];
         cpm_lagrange4<T>(__ldg(A.t + 3 * (int64_t)row), wx);
         cpm_lagrange4<T>(__ldg(A.t + 3 * (int64_t)row + 1), wy);
-        if (A.v.dim == 3) cpm_lagrange4<T>(__ldg(A.t + 3 * (int64_t)row + 2), wz);
+        if (DIM == 3) cpm_lagrange4<T>(__ldg(A.t + 3 * (int64_t)row + 2), wz);
         else { wz[0] = T(1); wz[1] = wz[2] = wz[3] = T(0); }
 #pragma unroll
         for (int q = 0; q < 4; ++q) s_wx[wib][lane][q] = wx[q];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) s_wyz[wib][lane][q] = wy[q & 3] * wz[q >> 2];
+        for (int q = 0; q < NL; ++q) s_wyz[wib][lane][q] = wy[q & 3] * wz[q >> 2];
       }
       __syncwarp();
-      T acc[CHUNK][RPL];
+      for (int grp = 0; grp < ngroups; ++grp) {
+        const int col = (grp * 32 + lane) * R;
+        const bool on = col < nrhs;
+        T uc[R];
 #pragma unroll
-      for (int j = 0; j < CHUNK; ++j)
+        for (int q = 0; q < R; ++q) uc[q] = T(0);
+        if (DIFF && on) vld<T, R>(u + (int64_t)base * ld_ + col, uc);
+#pragma unroll 1
+        for (int xp = 0; xp < XH; ++xp) {
+          T d[NL][NX][R];
 #pragma unroll
-        for (int q = 0; q < RPL; ++q) acc[j][q] = T(0);
-      if (on) {
-        for (int ln = 0; ln < nlines; ++ln) {
-          const int32_t s0 = s_line[wib][ln][0], s1 = s_line[wib][ln][1];
-          T d[4][RPL];
+          for (int ln = 0; ln < NL; ++ln) {
 #pragma unroll
-          for (int cx = 0; cx < 4; ++cx) {
-            int32_t stt = (cx < split) ? s0 : s1;
-            int32_t idx = (cx < split) ? (s0 + cx) : (s1 + (cx - split));
-            if (stt >= 0) {
-              ld<T, RPL>(u + (int64_t)idx * ld_ + col, d[cx]);
+            for (int q = 0; q < NX; ++q) {
+              const int32_t idx = s_idx[wib][ln * 4 + xp * NX + q];
+              if (on) {
+                vld<T, R>(u + (int64_t)idx * ld_ + col, d[ln][q]);
 #pragma unroll
-              for (int q = 0; q < RPL; ++q) if (DIFF) d[cx][q] -= uc[q];
-            } else {
+                for (int r = 0; r < R; ++r)
+                  if (DIFF) d[ln][q][r] -= uc[r];
+              } else {
 #pragma unroll
-              for (int q = 0; q < RPL; ++q) d[cx][q] = T(0);
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < CHUNK; ++j) {
-            if (j < k) {
-              const T wyz = s_wyz[wib][j][ln];
-              const T w0 = s_wx[wib][j][0], w1 = s_wx[wib][j][1], w2 = s_wx[wib][j][2], w3 = s_wx[wib][j][3];
-#pragma unroll
-              for (int q = 0; q < RPL; ++q) {
-                T line = w0 * d[0][q] + w1 * d[1][q] + w2 * d[2][q] + w3 * d[3][q];
-                acc[j][q] += wyz * line;
+                for (int r = 0; r < R; ++r) d[ln][q][r] = T(0);
               }
             }
           }
-        }
+#pragma unroll 1
+          for (int j = 0; j < k; ++j) {
+            T P[NX][R];
 #pragma unroll
-        for (int j = 0; j < CHUNK; ++j) {
-          if (j < k) {
-            const int64_t row = s_row[wib][j];
-            if (DIFF) {
-              T ui[RPL];
-              ld<T, RPL>(u + row * ld_ + col, ui);
+            for (int q = 0; q < NX; ++q)
 #pragma unroll
-              for (int q = 0; q < RPL; ++q) acc[j][q] += uc[q] - ui[q];
+              for (int r = 0; r < R; ++r) P[q][r] = T(0);
+#pragma unroll
+            for (int ln = 0; ln < NL; ++ln) {
+              const T w = s_wyz[wib][j][ln];
+#pragma unroll
+              for (int q = 0; q < NX; ++q)
+#pragma unroll
+                for (int r = 0; r < R; ++r) P[q][r] += w * d[ln][q][r];
             }
-            st<T, RPL>(a + row * ld_ + col, acc[j]);
+            T part[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) part[r] = T(0);
+#pragma unroll
+            for (int q = 0; q < NX; ++q) {
+              const T w = s_wx[wib][j][xp * NX + q];
+#pragma unroll
+              for (int r = 0; r < R; ++r) part[r] += w * P[q][r];
+            }
+            if (XH > 1 && xp > 0) {
+              const V pv = s_acc[(XH > 1) ? wib : 0][j][lane];
+              const T *pp = reinterpret_cast<const T *>(&pv);
+#pragma unroll
+              for (int r = 0; r < R; ++r) part[r] += pp[r];
+            }
+            if (XH > 1 && xp < XH - 1) {
+              V pv;
+              T *pp = reinterpret_cast<T *>(&pv);
+#pragma unroll
+              for (int r = 0; r < R; ++r) pp[r] = part[r];
+              s_acc[(XH > 1) ? wib : 0][j][lane] = pv;
+            } else if (on) {
+              const int64_t row = s_row[wib][j];
+              if (DIFF) {
+                T ui[R];
+                vld<T, R>(u + row * ld_ + col, ui);
+#pragma unroll
+                for (int r = 0; r < R; ++r) part[r] += uc[r] - ui[r];
+              }
+              vst<T, R>(a + row * ld_ + col, part);
+            }
           }
         }
       }
@@ -197,17 +292,65 @@ __global__ void __launch_bounds__(WARPS * 32) gather_cells_kernel(ApplyArgs<T> A
   }
 }
 
+// a_i += sum over the row's flipped entries of w (u_twin - u_node): one warp
+// per special row with flips, lanes over R adjacent columns
+template <typename T, int R>
+__global__ void __launch_bounds__(256) correct_kernel(const int32_t *__restrict__ crow,
+                                                      const int32_t *__restrict__ cstart,
+                                                      const int32_t *__restrict__ cnode,
+                                                      const int32_t *__restrict__ ccol, const T *__restrict__ cw,
+                                                      int64_t ncorr, const T *__restrict__ u, T *__restrict__ a,
+                                                      int nrhs, int64_t ld_) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int ngroups = (nrhs + 32 * R - 1) / (32 * R);
+  for (int64_t q = warp; q < ncorr; q += nwarps) {
+    const int64_t row = __ldg(crow + q);
+    const int32_t e0 = __ldg(cstart + q), e1 = __ldg(cstart + q + 1);
+    for (int grp = 0; grp < ngroups; ++grp) {
+      const int col = (grp * 32 + lane) * R;
+      if (col >= nrhs) continue;
+      T acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = T(0);
+      for (int32_t e = e0; e < e1; ++e) {
+        const T w = __ldg(cw + e);
+        T ut[R], un[R];
+        vld<T, R>(u + (int64_t)__ldg(ccol + e) * ld_ + col, ut);
+        vld<T, R>(u + (int64_t)__ldg(cnode + e) * ld_ + col, un);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] += w * (ut[r] - un[r]);
+      }
+      T av[R];
+      vld<T, R>(a + row * ld_ + col, av);
+#pragma unroll
+      for (int r = 0; r < R; ++r) av[r] += acc[r];
+      vst<T, R>(a + row * ld_ + col, av);
+    }
+  }
+}
+
 }  // namespace
+
+void cpm_free_cells(cpm_ctx *c) {
+  cudaFree(c->d_cell_start); cudaFree(c->d_cell_rows); cudaFree(c->d_cell_key); cudaFree(c->d_nbr8);
+  cudaFree(c->d_corr_row); cudaFree(c->d_corr_start); cudaFree(c->d_corr_node); cudaFree(c->d_corr_col);
+  cudaFree(c->d_corr_w64); cudaFree(c->d_corr_w32);
+  c->d_cell_start = nullptr; c->d_cell_rows = nullptr; c->d_cell_key = nullptr; c->d_nbr8 = nullptr;
+  c->d_corr_row = nullptr; c->d_corr_start = nullptr; c->d_corr_node = nullptr; c->d_corr_col = nullptr;
+  c->d_corr_w64 = nullptr; c->d_corr_w32 = nullptr;
+  c->ncells = 0; c->nbulk = 0; c->ncorr = 0; c->ncorr_ent = 0;
+}
 
 cpm_status cpm_build_cells(cpm_ctx *c) {
   cudaStream_t st = c->stream;
-  cudaFree(c->d_cell_start); cudaFree(c->d_cell_rows); cudaFree(c->d_cell_key);
-  c->d_cell_start = nullptr; c->d_cell_rows = nullptr; c->d_cell_key = nullptr;
-  c->ncells = 0;
-  c->nbulk = 0;
+  cpm_free_cells(c);
   const int64_t nkeys = c->nb * 512;
+  const int64_t nsp = std::max<int64_t>(c->nspec, 1);
   int32_t *count = nullptr, *offs = nullptr, *flag = nullptr, *cellpos = nullptr, *d_tot = nullptr;
-  int32_t h_tot = 0, h_cells = 0, nb32 = 0;
+  int32_t *ccnt = nullptr, *coffs = nullptr, *cflag = nullptr, *cpos = nullptr;
+  int32_t h_tot = 0, h_cells = 0, h_ent = 0, h_rows = 0;
   cpm_status rc = CPM_OK;
 #define TRY(x)                                             \
   do {                                                     \
@@ -229,7 +372,6 @@ cpm_status cpm_build_cells(cpm_ctx *c) {
   TRY(cudaStreamSynchronize(st));
   c->nbulk = h_tot;
   c->ncells = h_cells;
-  nb32 = h_tot;
   TRY(cudaMalloc(&c->d_cell_rows, sizeof(int32_t) * std::max<int64_t>(c->nbulk, 1)));
   TRY(cudaMalloc(&c->d_cell_start, sizeof(int32_t) * (c->ncells + 1)));
   TRY(cudaMalloc(&c->d_cell_key, sizeof(uint32_t) * std::max<int64_t>(c->ncells, 1)));
@@ -238,39 +380,90 @@ cpm_status cpm_build_cells(cpm_ctx *c) {
   cell_scatter_kernel<<<cpm_grid(c->NS, 256), 256, 0, st>>>(c->d_rbase, c->NS, flag, c->d_cell_rows);
   cell_finish_kernel<<<cpm_grid(nkeys, 256), 256, 0, st>>>(count, offs, cellpos, nkeys, c->d_cell_rows,
                                                            c->d_cell_start, c->d_cell_key);
-  TRY(cudaMemcpyAsync(c->d_cell_start + c->ncells, &nb32, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  set_i32_kernel<<<1, 1, 0, st>>>(c->d_cell_start + c->ncells, h_tot);
+  TRY(cudaMalloc(&c->d_nbr8, sizeof(int32_t) * 8 * std::max<int64_t>(c->NS, 1)));
+  nbr8_kernel<<<cpm_grid(c->NS, 256), 256, 0, st>>>(c->view(), c->d_rself, c->d_rbase, c->d_spec_of, c->d_spec_fcol,
+                                                    c->d_nbr8);
+  TRY(cudaGetLastError());
+  // flipped interpolation entries of the special rows
+  TRY(cudaMalloc(&ccnt, sizeof(int32_t) * nsp));
+  TRY(cudaMalloc(&coffs, sizeof(int32_t) * nsp));
+  TRY(cudaMalloc(&cflag, sizeof(int32_t) * nsp));
+  TRY(cudaMalloc(&cpos, sizeof(int32_t) * nsp));
+  if (c->nspec > 0) {
+    corr_count_kernel<<<cpm_grid(c->nspec, 128), 128, 0, st>>>(c->view(), c->d_spec_row, c->nspec, c->d_rbase,
+                                                               c->d_spec_ecol, ccnt);
+    TRY(cpm_exclusive_scan(ccnt, coffs, c->nspec, d_tot, st));
+    TRY(cudaMemcpyAsync(&h_ent, d_tot, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    flag_nonzero_kernel<<<cpm_grid(c->nspec, 256), 256, 0, st>>>(ccnt, c->nspec, cflag);
+    TRY(cpm_exclusive_scan(cflag, cpos, c->nspec, d_tot, st));
+    TRY(cudaMemcpyAsync(&h_rows, d_tot, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+  }
+  c->ncorr = h_rows;
+  c->ncorr_ent = h_ent;
+  TRY(cudaMalloc(&c->d_corr_row, sizeof(int32_t) * std::max<int64_t>(c->ncorr, 1)));
+  TRY(cudaMalloc(&c->d_corr_start, sizeof(int32_t) * (c->ncorr + 1)));
+  TRY(cudaMalloc(&c->d_corr_node, sizeof(int32_t) * std::max<int64_t>(c->ncorr_ent, 1)));
+  TRY(cudaMalloc(&c->d_corr_col, sizeof(int32_t) * std::max<int64_t>(c->ncorr_ent, 1)));
+  TRY(cudaMalloc(&c->d_corr_w64, sizeof(double) * std::max<int64_t>(c->ncorr_ent, 1)));
+  TRY(cudaMalloc(&c->d_corr_w32, sizeof(float) * std::max<int64_t>(c->ncorr_ent, 1)));
+  set_i32_kernel<<<1, 1, 0, st>>>(c->d_corr_start + c->ncorr, h_ent);
+  if (c->ncorr > 0)
+    corr_fill_kernel<<<cpm_grid(c->nspec, 128), 128, 0, st>>>(c->view(), c->d_spec_row, c->nspec, c->d_rbase,
+                                                              c->d_spec_ecol, c->d_spec_ew, ccnt, coffs, cpos,
+                                                              c->d_corr_row, c->d_corr_start, c->d_corr_node,
+                                                              c->d_corr_col, c->d_corr_w64, c->d_corr_w32);
   TRY(cudaGetLastError());
   TRY(cudaStreamSynchronize(st));
 done:
 #undef TRY
   cudaFree(count); cudaFree(offs); cudaFree(flag); cudaFree(cellpos); cudaFree(d_tot);
+  cudaFree(ccnt); cudaFree(coffs); cudaFree(cflag); cudaFree(cpos);
+  if (rc != CPM_OK) cpm_free_cells(c);
   return rc;
 }
 
-template <typename T>
-void cpm_launch_gather_cells(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld,
-                             cudaStream_t st, bool diff) {
-  if (c->ncells == 0) return;
-  unsigned g = (unsigned)std::min<int64_t>((c->ncells + WARPS - 1) / WARPS, 152 * 8);
+template <typename T, bool DIFF, int DIM, int R>
+static void launch_cells_k(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld,
+                           cudaStream_t st) {
+  // x positions per pass: node values of one pass stay near 64 registers
+  constexpr int XH = (sizeof(T) == 8) ? ((R == 2) ? 4 : 2) : 2;
+  unsigned g = (unsigned)std::min<int64_t>((c->ncells + WARPS - 1) / WARPS, 152 * 16);
   if (g < 1) g = 1;
-  const int rpl = (nrhs > 32) ? 2 : 1;
-  if (rpl == 2) {
-    if (diff)
-      gather_cells_kernel<T, true, 2><<<g, WARPS * 32, 0, st>>>(A, c->d_cell_start, c->d_cell_key, c->d_cell_rows,
-                                                               c->ncells, u, a, nrhs, ld);
-    else
-      gather_cells_kernel<T, false, 2><<<g, WARPS * 32, 0, st>>>(A, c->d_cell_start, c->d_cell_key, c->d_cell_rows,
-                                                                c->ncells, u, a, nrhs, ld);
+  gather_cells_kernel<T, DIFF, DIM, XH, R><<<g, WARPS * 32, 0, st>>>(A, c->d_cell_start, c->d_cell_key,
+                                                                    c->d_cell_rows, c->ncells, u, a, nrhs, ld);
+}
+
+template <typename T, int R>
+static void launch_cells_r(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld,
+                           cudaStream_t st, bool diff) {
+  if (c->dim == 3) {
+    if (diff) launch_cells_k<T, true, 3, R>(c, A, u, a, nrhs, ld, st);
+    else launch_cells_k<T, false, 3, R>(c, A, u, a, nrhs, ld, st);
   } else {
-    if (diff)
-      gather_cells_kernel<T, true, 1><<<g, WARPS * 32, 0, st>>>(A, c->d_cell_start, c->d_cell_key, c->d_cell_rows,
-                                                               c->ncells, u, a, nrhs, ld);
-    else
-      gather_cells_kernel<T, false, 1><<<g, WARPS * 32, 0, st>>>(A, c->d_cell_start, c->d_cell_key, c->d_cell_rows,
-                                                                c->ncells, u, a, nrhs, ld);
+    if (diff) launch_cells_k<T, true, 2, R>(c, A, u, a, nrhs, ld, st);
+    else launch_cells_k<T, false, 2, R>(c, A, u, a, nrhs, ld, st);
+  }
+  if (c->ncorr > 0) {
+    const T *cw;
+    if constexpr (sizeof(T) == 8) cw = reinterpret_cast<const T *>(c->d_corr_w64);
+    else cw = reinterpret_cast<const T *>(c->d_corr_w32);
+    unsigned gc = (unsigned)std::min<int64_t>((c->ncorr + 7) / 8, 152 * 16);
+    correct_kernel<T, R><<<gc, 256, 0, st>>>(c->d_corr_row, c->d_corr_start, c->d_corr_node, c->d_corr_col, cw,
+                                             c->ncorr, u, a, nrhs, ld);
   }
 }
-template void cpm_launch_gather_cells<float>(const cpm_ctx *, const ApplyArgs<float> &, const float *, float *, int,
-                                             int64_t, cudaStream_t, bool);
-template void cpm_launch_gather_cells<double>(const cpm_ctx *, const ApplyArgs<double> &, const double *, double *,
-                                              int, int64_t, cudaStream_t, bool);
+
+template <typename T>
+int cpm_launch_gather_cells(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld,
+                            cudaStream_t st, bool diff, int rpl) {
+  if (c->ncells == 0) return 0;
+  if (rpl == 2) launch_cells_r<T, 2>(c, A, u, a, nrhs, ld, st, diff);
+  else launch_cells_r<T, 1>(c, A, u, a, nrhs, ld, st, diff);
+  return (c->ncorr > 0) ? 2 : 1;
+}
+template int cpm_launch_gather_cells<float>(const cpm_ctx *, const ApplyArgs<float> &, const float *, float *, int,
+                                            int64_t, cudaStream_t, bool, int);
+template int cpm_launch_gather_cells<double>(const cpm_ctx *, const ApplyArgs<double> &, const double *, double *,
+                                             int, int64_t, cudaStream_t, bool, int);

@@ -131,12 +131,23 @@ struct cpm_ctx {
   double *d_spec_ew = nullptr;     // [nspec*64]
   float *d_spec_ew32 = nullptr;    // [nspec*64]
   int32_t *d_spec_fcol = nullptr;  // [nspec*6]
+  // PDE rows bucketed by their stencil base node ("cells"), for the batched products
+  int64_t ncells = 0, nbulk = 0;
+  int32_t *d_cell_start = nullptr;  // [ncells+1]
+  int32_t *d_cell_rows = nullptr;   // [nbulk] (nbulk = NS)
+  uint32_t *d_cell_key = nullptr;   // [ncells] packed base location (brick << 9 | local)
+  int32_t *d_nbr8 = nullptr;        // [NS][8] FD neighbour columns (6 used; flipped near curves)
+  // flipped interpolation entries of the special rows: row i's E entry at node
+  // corr_node holds column corr_col instead (a BC DOF), weight corr_w
+  int64_t ncorr = 0, ncorr_ent = 0;
+  int32_t *d_corr_row = nullptr;    // [ncorr]
+  int32_t *d_corr_start = nullptr;  // [ncorr+1]
+  int32_t *d_corr_node = nullptr;   // [ncorr_ent]
+  int32_t *d_corr_col = nullptr;    // [ncorr_ent]
+  double *d_corr_w64 = nullptr;     // [ncorr_ent]
+  float *d_corr_w32 = nullptr;      // [ncorr_ent]
   // transposed structure (adjoint)
   bool transpose_ready = false;
-  int64_t ncells = 0, nbulk = 0;    // bulk rows bucketed by their stencil base node
-  int32_t *d_cell_start = nullptr;  // [ncells+1]
-  int32_t *d_cell_rows = nullptr;   // [nbulk]
-  uint32_t *d_cell_key = nullptr;   // [ncells] packed base location (brick << 9 | local)
   int64_t nT = 0;                   // explicit transposed entries (special E/FD rows, BC rows)
   int32_t *d_T_ptr = nullptr;       // [N+1] CSR over columns
   int32_t *d_T_row = nullptr;       // [nT] source row
@@ -181,6 +192,7 @@ cpm_status cpm_ensure(WorkBuf &b, size_t bytes);
 void cpm_free_boundary(cpm_ctx *c);
 cpm_status cpm_build_transpose(cpm_ctx *c);
 cpm_status cpm_build_cells(cpm_ctx *c);
+void cpm_free_cells(cpm_ctx *c);
 
 static inline unsigned cpm_grid(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;

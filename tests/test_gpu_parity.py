@@ -72,10 +72,11 @@ def test_apply_fp32_and_batched(oracle_mod, torch_mod, name):
 
 
 @pytest.mark.parametrize("name", ["circle_dir2", "sphere_lat_dir2", "torus_mer_dir2"])
-@pytest.mark.parametrize("nrhs", [20, 40, 64])
+@pytest.mark.parametrize("nrhs", [20, 33, 40, 64])
 def test_apply_warp_per_row_batches(oracle_mod, torch_mod, name, nrhs):
-    """Batched products (one warp per row, lanes over right-hand sides) in FP64
-    and FP32 against the oracle's assembled A, column by column."""
+    """Batched products (cell-bucketed gather with the flipped-entry correction,
+    warp-per-row combine; 33 columns take the per-element path) in FP64 and
+    FP32 against the oracle's assembled A, column by column."""
     torch = torch_mod
     w = SMALL[name]()
     band, ref = pair(oracle_mod, w)
