@@ -7,7 +7,8 @@ Default workload (one step), the unit-sphere configuration at h = 1/128
 with a batch of 64 Poisson problems -Delta_S u = l(l+1) Y_l^m, the circles
 carrying Y_l^m, for the first 64 real spherical harmonics with 1 <= l <= 8
 (the exact solution of column k is Y_l^m itself).  One step solves the 64
-together with FP32 BiCGSTAB and FP64 reliable updates to a Jacobi-scaled
+together by mixed-precision iterative refinement (FP32 BiCGSTAB inner solves, FP64
+residuals and solution) to a Jacobi-scaled
 relative residual of 1e-10.  The metric is seconds per right-hand side.
 Alongside: the plain FP64 solve of one right-hand side of the same workload,
 the single-RHS operator product's algorithmic bandwidth against the measured
@@ -99,11 +100,11 @@ class Workload:
         if self.kind == "sphere":
             wl = (f"unit sphere, h=1/{round(1 / self.h)}, Dirichlet circles theta=pi/4, 3pi/4; {NRHS} Poisson "
                   f"problems -Delta u = l(l+1) Y_l^m with the circles carrying Y_l^m (first {NRHS} real harmonics, "
-                  f"1<=l<=8); batched FP32 BiCGSTAB with FP64 reliable updates to a Jacobi-scaled relative residual "
+                  f"1<=l<=8); batched mixed-precision refinement (FP32 BiCGSTAB inner solves, FP64 residuals) to a Jacobi-scaled relative residual "
                   f"of {TOL:g}")
         else:
             wl = (f"torus R=1 r=0.4, h=1/{round(1 / self.h)}, 8 Dirichlet meridians (seeded angles, min gap 0.2 "
-                  f"rad), {NRHS} right-hand sides U[0,1]; batched FP32 BiCGSTAB with FP64 reliable updates to a "
+                  f"rad), {NRHS} right-hand sides U[0,1]; batched mixed-precision refinement (FP32 BiCGSTAB inner solves) to a "
                   f"Jacobi-scaled relative residual of {TOL:g}")
         d = {"workload": wl, "nrhs": NRHS, "tol": TOL, "norm": "Jacobi-scaled residual",
              "l2": "inputs larger than L2 (each [N][64] Krylov vector is several hundred MB vs 129 MB L2)"}

@@ -105,19 +105,18 @@ typedef struct {
                         CPM_NORM_SCALED, the default) or the identity (CPM_NORM_PLAIN) */
   int maxit;         /* BiCGSTAB iterations (both modes) */
   int mode;          /* cpm_solve_mode */
-  double inner_tol;  /* FP32_IR: reliable-update factor delta in (0,1): the FP32 correction is
-                        folded into the FP64 solution and the FP64 residual recomputed once the
-                        FP32 recursive residual has dropped by delta (0 -> 0.1) */
-  int max_refine;    /* FP32_IR: maximum number of FP64 folds (0 -> 200) */
+  double inner_tol;  /* FP32_IR: relative tolerance in (0,1) of each FP32 inner solve, i.e. the
+                        residual reduction one refinement step aims for (0 -> 1e-2) */
+  int max_refine;    /* FP32_IR: maximum number of refinement steps (0 -> 200) */
   int check_every;   /* iterations between host convergence checks (0 -> 16) */
   int norm;          /* cpm_norm.  SCALED iterates on the row-scaled system W A x = W f; PLAIN is
                         the paper's right-preconditioned form with the unscaled residual */
-  int inner_maxit;   /* FP32_IR: fold at least every this many iterations (0 -> 1000) */
+  int inner_maxit;   /* FP32_IR: iteration limit of one inner solve (0 -> 1000) */
 } cpm_solve_opts;
 
 typedef struct {
   int iterations;    /* BiCGSTAB iterations */
-  int refinements;   /* FP32_IR: FP64 folds (refinement steps) taken */
+  int refinements;   /* FP32_IR: refinement steps taken */
   int restarts;      /* shadow-residual restarts after near breakdown */
   double relres;     /* final FP64 relative residual |W (f - A x)| / |W f| in the chosen norm (max over
                         right-hand sides) */
@@ -185,11 +184,13 @@ cpm_status cpm_extend(cpm_ctx *ctx, const double *u_dev, double *a_dev, int nrhs
 
 /* Solves A x = f with diagonal-preconditioned BiCGSTAB (Sec. 5.4), preconditioner
  * diag(m I + n diag L) on PDE rows and 1 on BC rows.  x_dev holds the initial
- * guess on entry.  FP64 mode iterates in FP64; FP32_IR iterates in FP32 and
- * refines in FP64: the FP32 correction is folded into the FP64 solution and the
- * FP64 residual replaces the FP32 recursive one at each reliable update; a
- * right-hand side whose FP32 phase stops gaining is finished by FP64 BiCGSTAB
- * from its current iterate, so the result always meets tol in FP64.  All right-hand
+ * guess on entry.  FP64 mode iterates in FP64.  FP32_IR is mixed-precision
+ * iterative refinement: each step computes the FP64 residual r = f - A x,
+ * solves A d = r with FP32 BiCGSTAB (FP32 operator and Krylov vectors, d
+ * accumulated in FP64) to the relative inner_tol, and adds d to x in FP64 where
+ * that lowers the FP64 residual; a right-hand side whose FP32 steps stop gaining
+ * is finished by FP64 BiCGSTAB from its current iterate, so the result always
+ * meets tol in FP64.  All right-hand
  * sides of a batch iterate together with their own scalars.  The first call with
  * a given nrhs allocates its workspace inside the context.  Synchronises
  * `stream`.  stats may be NULL.  Errors: ARG, STATE, OOM, CUDA, BREAKDOWN,

@@ -1,5 +1,5 @@
-// krylov.cu -- preconditioned BiCGSTAB on the device (Sec. 5.4), in FP64 or in
-// FP32 with FP64 reliable updates.
+// krylov.cu -- preconditioned BiCGSTAB on the device (Sec. 5.4), in FP64 or as
+// FP32 inner solves of a mixed-precision iterative refinement.
 //
 // The solver is van der Vorst's BiCGSTAB with the diagonal of m I + n diag(L)
 // on PDE rows and 1 on BC rows as preconditioner (Sec. 5.4).  Two forms:
@@ -15,20 +15,21 @@
 // tolerance is frozen.  A near-zero rho restarts that right-hand side's shadow
 // residual (r_hat = r); too many restarts is a breakdown.
 //
-// The FP32 form (iterative refinement in its "reliable update" shape): the
-// Krylov vectors and the operator are FP32, the solution x and the true
-// residual f - A x are FP64.  The FP32 iterate is a correction that is folded
-// into x whenever the FP32 recursive residual has dropped by a factor delta
-// since the last fold (or after a fixed number of iterations); then the FP64
-// residual is recomputed and replaces the FP32 recursive one.  Unlike
-// restarting an inner solve at every refinement, the Krylov recurrences
-// continue across folds, so the slowly converging smooth modes keep their
-// progress.  Convergence is decided on the FP64 residual only.
+// The FP32 form is mixed-precision iterative refinement: the solution x and
+// the residual f - A x are FP64; each outer step solves for a correction with
+// FP32 BiCGSTAB (FP32 operator in its difference form and FP32 Krylov vectors,
+// the correction itself accumulated in FP64) and adds it to x.  Storing a
+// smooth field in FP32 limits the FP32 operator's relative accuracy to about
+// eps_32 / h^2 times the field-to-Laplacian ratio, so each outer step targets
+// a modest reduction (1e-2 by default) and starts a fresh Krylov space.
+// Convergence is decided on the FP64 residual only; a column that the FP32
+// steps stop improving finishes in FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "apply.cuh"
@@ -91,7 +92,7 @@ __global__ void reduce_parts_kernel(const double *part, int nblocks, int nq, int
 //                      [8] |W f|^2 [9] |r|^2 (recursive) [10] breakdown
 //                      [11] best |r|^2 [12] iterations since |r| last halved
 //                      [13] stopped without reaching tol (stall or divergence)
-//                      [14] |r|^2 at the last reliable update (FP32 form)
+//                      [14] |r|^2 at the start
 constexpr int NSC = 15;
 
 __global__ void scal_init_kernel(double *sc, const double *dots /* (r,r),(f,f) */, int nrhs, double tol) {
@@ -163,38 +164,6 @@ __global__ void scal_conv_kernel(double *sc, const double *dots, int nrhs, doubl
   else { s[12] += 1.0; if (decide && s[12] > stall) { s[13] = 1.0; s[5] = 0.0; } }
 }
 
-// FP32 form: after a reliable update, per column: new |r|^2, activity, and a
-// restart of the recurrences for columns that broke down
-__global__ void scal_reliable_kernel(double *sc, const double *rn2, const double *act, const double *replaced,
-                                     const double *reset, int nrhs) {
-  int r = threadIdx.x;
-  if (r >= nrhs) return;
-  double *s = sc + r * NSC;
-  s[5] = act[r];
-  if (replaced[r] != 0.0 && rn2[r] >= 0.0) {
-    s[9] = rn2[r];
-    s[14] = rn2[r];
-    if (rn2[r] < s[11]) { s[11] = rn2[r]; s[12] = 0.0; }
-  }
-  if (reset[r] != 0.0) {
-    s[0] = 1.0; s[1] = 1.0; s[2] = 1.0; s[6] = 0.0; s[10] = 0.0; s[13] = 0.0;
-    s[7] += 1.0;
-  }
-}
-
-// FP32 form with a measuring norm other than the iteration's: set |r|^2 of the
-// replaced columns from a fresh dot product
-__global__ void scal_setr_kernel(double *sc, const double *dots, const double *replaced, int nrhs) {
-  int r = threadIdx.x;
-  if (r >= nrhs) return;
-  if (replaced[r] == 0.0) return;
-  double *s = sc + r * NSC;
-  s[9] = dots[r];
-  s[14] = dots[r];
-  s[11] = dots[r];
-  s[12] = 0.0;
-}
-
 // ---- fused vector updates ---------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T dinv_of(int64_t i, int64_t NS, T dS) { return (i < NS) ? dS : T(1); }
@@ -251,9 +220,11 @@ __global__ void upd_s_kernel(const double *sc, int64_t N, int64_t NS, int nrhs, 
 }
 
 // x += alpha ph + omega sh;  r = s - omega t
-template <typename T>
-__global__ void upd_xr_kernel(const double *sc, int64_t N, int nrhs, int64_t ld, T *x, T *r, const T *ph, const T *sh,
-                              const T *s_, const T *t) {
+// (x may be kept in a wider type TX than the Krylov vectors: the increment is
+// formed in T and accumulated in TX)
+template <typename T, typename TX>
+__global__ void upd_xr_kernel(const double *sc, int64_t N, int nrhs, int64_t ld, TX *x, T *r, const T *ph,
+                              const T *sh, const T *s_, const T *t) {
   for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
        tid += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = tid / nrhs;
@@ -262,7 +233,7 @@ __global__ void upd_xr_kernel(const double *sc, int64_t N, int nrhs, int64_t ld,
     if (s[5] == 0.0) continue;
     int64_t o = i * ld + c;
     T al = T(s[1]), om = T(s[2]);
-    x[o] = x[o] + al * ph[o] + om * sh[o];
+    x[o] = x[o] + TX(al * ph[o] + om * sh[o]);
     r[o] = s_[o] - om * t[o];
   }
 }
@@ -307,48 +278,41 @@ __global__ void scale_rows64_kernel(int64_t N, int64_t NS, int nrhs, int64_t ld,
   }
 }
 
-// candidate of a reliable update: xc = x + x32 (every column)
-__global__ void candidate_kernel(int64_t N, int nrhs, int64_t ld, const double *x, const float *x32, double *xc) {
-  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = tid / nrhs;
-    int c = (int)(tid - i * nrhs);
-    int64_t o = i * ld + c;
-    xc[o] = x[o] + (double)x32[o];
-  }
-}
-
-// columns with acc != 0 take the candidate; columns with drop != 0 restart x32
-__global__ void accept_kernel(int64_t N, int nrhs, int64_t ld, const double *acc, const double *drop,
-                              const double *xc, double *x, float *x32) {
+// columns with acc != 0 take the candidate
+__global__ void accept_kernel(int64_t N, int nrhs, int64_t ld, const double *acc, const double *xc, double *x) {
   for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
        tid += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = tid / nrhs;
     int c = (int)(tid - i * nrhs);
     int64_t o = i * ld + c;
     if (acc[c] != 0.0) x[o] = xc[o];
-    if (drop[c] != 0.0) x32[o] = 0.0f;
   }
 }
 
-// r32 = W r64 for the active columns; columns that restart also take
-// rhat = r32 and p = v = 0
-__global__ void replace_r_kernel(int64_t N, int64_t NS, double wrow, float mix, int nrhs, int64_t ld,
-                                 const double *act, const double *reset, const double *r64, float *r32, float *rh,
-                                 float *p, float *v) {
+// restarted refinement: FP32 right-hand side W r / |W r| per active column
+// (scale 0: inactive column, zero right-hand side)
+__global__ void ir_rhs_kernel(int64_t N, int64_t NS, double wrow, int nrhs, int64_t ld, const double *scale,
+                              const double *r64, float *f32) {
   for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
        tid += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = tid / nrhs;
     int c = (int)(tid - i * nrhs);
-    if (act[c] == 0.0) continue;
     int64_t o = i * ld + c;
-    float rv = (float)(((i < NS) ? wrow : 1.0) * r64[o]);
-    r32[o] = rv;
-    if (reset[c] != 0.0) {
-      rh[o] = rv * shadow_weight(i, c, mix);
-      p[o] = 0.0f;
-      v[o] = 0.0f;
-    }
+    double sc = scale[c];
+    f32[o] = (sc > 0.0) ? (float)(((i < NS) ? wrow : 1.0) * r64[o] / sc) : 0.0f;
+  }
+}
+
+// candidate xc = x + scale * d (FP64 accumulation of the FP32 correction)
+__global__ void ir_candidate_kernel(int64_t N, int nrhs, int64_t ld, const double *scale, const double *d,
+                                    const double *x, double *xc) {
+  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
+       tid += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = tid / nrhs;
+    int c = (int)(tid - i * nrhs);
+    int64_t o = i * ld + c;
+    double sc = scale[c];
+    xc[o] = (sc > 0.0) ? x[o] + sc * d[o] : x[o];
   }
 }
 
@@ -363,7 +327,8 @@ struct SolveWork {
   void *vec[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double *r64 = nullptr;    // FP64 true residual
   double *fs = nullptr;     // W f (scaled FP64 form)
-  float *x32 = nullptr;     // FP32 correction since the last reliable update
+  float *f32 = nullptr;     // FP32 right-hand side of the inner solves
+  double *xd = nullptr;     // FP64 solution of the inner solves
   double *part = nullptr, *dots = nullptr, *sc = nullptr;
   double *h_pinned = nullptr;  // host mirror of sc
   double *d_cols = nullptr;    // per-column host-set arrays: [4][nrhs]
@@ -372,7 +337,7 @@ struct SolveWork {
 static void free_work(SolveWork *w) {
   if (!w) return;
   for (auto &p : w->vec) cudaFree(p);
-  cudaFree(w->r64); cudaFree(w->fs); cudaFree(w->x32);
+  cudaFree(w->r64); cudaFree(w->fs); cudaFree(w->f32); cudaFree(w->xd);
   cudaFree(w->part); cudaFree(w->dots); cudaFree(w->sc); cudaFree(w->d_cols);
   if (w->h_pinned) cudaFreeHost(w->h_pinned);
   delete w;
@@ -399,7 +364,10 @@ static cpm_status get_work(cpm_ctx *c, SolveWork *&w, int64_t N, int nrhs, int64
   for (auto &p : w->vec) CPM_CUDA_TRY(cudaMalloc(&p, vb));
   CPM_CUDA_TRY(cudaMalloc(&w->r64, (size_t)N * ld * sizeof(double)));
   CPM_CUDA_TRY(cudaMalloc(&w->fs, (size_t)N * ld * sizeof(double)));
-  if (elem == (int)sizeof(float)) CPM_CUDA_TRY(cudaMalloc(&w->x32, (size_t)N * ld * sizeof(float)));
+  if (elem == (int)sizeof(float)) {
+    CPM_CUDA_TRY(cudaMalloc(&w->f32, (size_t)N * ld * sizeof(float)));
+    CPM_CUDA_TRY(cudaMalloc(&w->xd, (size_t)N * ld * sizeof(double)));
+  }
   CPM_CUDA_TRY(cudaMalloc(&w->part, sizeof(double) * RED_BLOCKS * 3 * nrhs));
   CPM_CUDA_TRY(cudaMalloc(&w->dots, sizeof(double) * 3 * nrhs));
   CPM_CUDA_TRY(cudaMalloc(&w->sc, sizeof(double) * NSC * nrhs));
@@ -431,8 +399,8 @@ struct KrylovForm {
 };
 
 // one BiCGSTAB iteration for all active columns (device only)
-template <typename T>
-static cpm_status iteration(cpm_ctx *c, ApplyFn<T> apply, const KrylovForm &form, double m, double n, T *x,
+template <typename T, typename TX = T>
+static cpm_status iteration(cpm_ctx *c, ApplyFn<T> apply, const KrylovForm &form, double m, double n, TX *x,
                             SolveWork *w, double tol, int decide, cudaStream_t st) {
   const int64_t N = c->NS + c->NC, NS = c->NS;
   const int nrhs = w->nrhs;
@@ -453,7 +421,7 @@ static cpm_status iteration(cpm_ctx *c, ApplyFn<T> apply, const KrylovForm &form
   if (rc) return rc;
   dots<T>(w, 2, t, s, t, t, nullptr, nullptr, N, st);
   scal_omega_kernel<<<1, 256, 0, st>>>(w->sc, w->dots, nrhs);
-  upd_xr_kernel<T><<<g, 256, 0, st>>>(w->sc, N, nrhs, ld, x, r, ph, sh, s, t);
+  upd_xr_kernel<T, TX><<<g, 256, 0, st>>>(w->sc, N, nrhs, ld, x, r, ph, sh, s, t);
   dots<T>(w, 1, r, r, nullptr, nullptr, nullptr, nullptr, N, st);
   scal_conv_kernel<<<1, 256, 0, st>>>(w->sc, w->dots, nrhs, tol, form.stall, decide);
   cpm_count_launches(c, 7);  // 4 scalar + 3 vector kernels (products and dots count themselves)
@@ -467,17 +435,24 @@ static cpm_status read_scalars(SolveWork *w, cudaStream_t st) {
 }
 
 // BiCGSTAB on A x = f in one precision T; x holds the initial guess.
-template <typename T>
-static cpm_status bicgstab(cpm_ctx *c, ApplyFn<T> apply, const KrylovForm &form, double m, double n, const T *f, T *x,
-                           SolveWork *w, double tol, int maxit, int check_every, int *iters, int *restarts,
+// (x of a wider type TX than T requires x = 0 on entry: the initial product
+// is skipped)
+template <typename T, typename TX = T>
+static cpm_status bicgstab(cpm_ctx *c, ApplyFn<T> apply, const KrylovForm &form, double m, double n, const T *f,
+                           TX *x, SolveWork *w, double tol, int maxit, int check_every, int *iters, int *restarts,
                            bool *broke, cudaStream_t st) {
   const int64_t N = c->NS + c->NC;
   const int nrhs = w->nrhs;
   const int64_t ld = w->ld;
   T *r = (T *)w->vec[0], *rh = (T *)w->vec[1], *p = (T *)w->vec[2], *v = (T *)w->vec[3];
   const unsigned g = cpm_grid(N * nrhs, 256);
-  cpm_status rc = apply(c, m, n, form.rowscale, x, r, nrhs, ld, st);
-  if (rc) return rc;
+  cpm_status rc = CPM_OK;
+  if constexpr (std::is_same<T, TX>::value) {
+    rc = apply(c, m, n, form.rowscale, x, r, nrhs, ld, st);
+    if (rc) return rc;
+  } else {
+    CPM_CUDA_TRY(cudaMemsetAsync(r, 0, sizeof(T) * (size_t)N * ld, st));
+  }
   init_r_kernel<T><<<g, 256, 0, st>>>(N, nrhs, ld, f, r, rh, p, v);
   cpm_count_launches(c, 1);
   dots<T>(w, 2, r, r, f, f, nullptr, nullptr, N, st);
@@ -500,7 +475,7 @@ static cpm_status bicgstab(cpm_ctx *c, ApplyFn<T> apply, const KrylovForm &form,
     if (!any || it >= maxit) break;
     int steps = std::min(check_every, maxit - it);
     for (int k = 0; k < steps; ++k) {
-      rc = iteration<T>(c, apply, form, m, n, x, w, tol, 1, st);
+      rc = iteration<T, TX>(c, apply, form, m, n, x, w, tol, 1, st);
       if (rc) return rc;
     }
     CPM_CUDA_TRY(cudaGetLastError());
@@ -540,191 +515,96 @@ static double worst_relres(const std::vector<double> &rn2, const std::vector<dou
   return worst;
 }
 
-// FP32 BiCGSTAB with FP64 reliable updates (see the file comment)
-static cpm_status bicgstab_reliable(cpm_ctx *c, ApplyFn<double> ap64, ApplyFn<float> ap32, const KrylovForm &form,
-                                    double m, double n, const double *f, double *x, SolveWork *w, double wrow,
-                                    double wfp32,
-                                    double tol, double delta, int max_between, int maxit, int max_updates,
-                                    int check_every, bool trace, int *iters, int *updates, int *restarts, bool *broke,
-                                    std::vector<double> &rn2, std::vector<double> &fn2, cudaStream_t st) {
+// Mixed-precision iterative refinement with restarted inner solves: each
+// outer step takes the FP64 residual r = f - A x, solves (W A) d = W r / |W r|
+// by FP32 BiCGSTAB from d = 0 to the relative inner tolerance, and adds
+// |W r| d to x in FP64.  Every inner solve starts a fresh Krylov space, so a
+// loss of accuracy in one FP32 solve does not carry into the next.  A column
+// whose FP64 residual fails to halve over two outer steps is left for the
+// FP64 finish.
+static cpm_status ir_restarted(cpm_ctx *c, ApplyFn<double> ap64, ApplyFn<float> ap32, const KrylovForm &form32,
+                               double m, double n, const double *f, double *x, SolveWork *w, double wrow, double dS,
+                               double tol, double inner_tol, int inner_maxit, int maxit, int max_outer,
+                               int check_every, bool trace, int *iters, int *outers, int *restarts,
+                               std::vector<double> &rn2, std::vector<double> &fn2, cudaStream_t st) {
   const int64_t N = c->NS + c->NC;
   const int nrhs = w->nrhs;
   const int64_t ld = w->ld;
-  float *r = (float *)w->vec[0], *rh = (float *)w->vec[1], *p = (float *)w->vec[2], *v = (float *)w->vec[3];
-  float *x32 = w->x32;
   const unsigned g = cpm_grid(N * nrhs, 256);
-  double *d_rn2 = w->d_cols, *d_act = w->d_cols + nrhs, *d_reset = w->d_cols + 2 * nrhs;
-  std::vector<double> act(nrhs, 1.0), reset(nrhs, 1.0), best(nrhs, INFINITY);
-  std::vector<int> since_best(nrhs, 0);
+  double *d_scale = w->d_cols;
+  std::vector<double> scale(nrhs, 0.0), best(nrhs, INFINITY);
+  std::vector<int> stall(nrhs, 0);
+  std::vector<char> act(nrhs, 1);
   cpm_status rc = residual64(c, ap64, m, n, f, x, w, wrow, rn2, fn2, st);
   if (rc) return rc;
-  CPM_CUDA_TRY(cudaMemsetAsync(x32, 0, sizeof(float) * (size_t)N * ld, st));
-  // scalars: |W f|^2 from the FP64 pass, |r|^2 from the replaced residual
-  CPM_CUDA_TRY(cudaMemcpyAsync(w->dots, rn2.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-  CPM_CUDA_TRY(cudaMemcpyAsync(w->dots + nrhs, fn2.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-  scal_init_kernel<<<1, 256, 0, st>>>(w->sc, w->dots, nrhs, 0.0);
-  cpm_count_launches(c, 1);
-  int it = 0, last_update = 0, nupd = 0, nrestart = 0;
-  *broke = false;
-  bool do_update = true;  // the first "update" installs r32 = W r64, rhat = r32
-  std::vector<double> acc(nrhs, 0.0), replace(nrhs, 1.0), drop(nrhs, 0.0);
-  std::vector<int> nreject(nrhs, 0);
-  while (true) {
-    if (do_update) {
-      if (nupd > 0) {
-        // fold x32 into x only where the FP64 residual of x + x32 decreased;
-        // elsewhere the correction is dropped and the recurrences restart
-        candidate_kernel<<<g, 256, 0, st>>>(N, nrhs, ld, x, x32, w->fs);
-        cpm_count_launches(c, 1);
-        std::vector<double> rn2_prev = rn2;
-        rc = residual64(c, ap64, m, n, f, w->fs, w, wrow, rn2, fn2, st);
-        if (rc) return rc;
-        bool rejected = false;
-        for (int q = 0; q < nrhs; ++q) {
-          bool ok = act[q] != 0.0 && std::isfinite(rn2[q]) && rn2[q] < rn2_prev[q];
-          acc[q] = ok ? 1.0 : 0.0;
-          if (ok) {
-            nreject[q] = 0;
-            replace[q] = 1.0;
-          } else if (act[q] != 0.0) {
-            // not folded: BiCGSTAB spikes are often temporary, so the FP32
-            // iteration goes on unchanged; after three rejections in a row the
-            // correction is dropped and the recurrences restart from x
-            rejected = true;
-            replace[q] = 0.0;
-            if (++nreject[q] >= 3) {
-              nreject[q] = 0;
-              reset[q] = 1.0;
-              replace[q] = 1.0;
-              ++nrestart;
-            }
-            if (trace && q == 0)
-              std::fprintf(stderr, "[cpm reliable] column 0: fold rejected (fp32 |r|/|r0| %.3e)%s\n",
-                           std::sqrt(w->h_pinned[9] / w->h_pinned[14]), reset[q] != 0.0 ? ", restart" : "");
-          }
-        }
-        // x takes the candidate where accepted; x32 restarts where accepted or
-        // reset (a reset column also needs its residual replaced)
-        for (int q = 0; q < nrhs; ++q) {
-          drop[q] = (acc[q] != 0.0 || reset[q] != 0.0) ? 1.0 : 0.0;
-          if (reset[q] != 0.0) replace[q] = 1.0;
-        }
-        CPM_CUDA_TRY(cudaMemcpyAsync(d_act, acc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-        CPM_CUDA_TRY(cudaMemcpyAsync(d_reset, drop.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-        accept_kernel<<<g, 256, 0, st>>>(N, nrhs, ld, d_act, d_reset, w->fs, x, x32);
-        cpm_count_launches(c, 1);
-        if (rejected) {
-          rc = residual64(c, ap64, m, n, f, x, w, wrow, rn2, fn2, st);
-          if (rc) return rc;
-        }
-      }
-      bool any = false;
-      for (int q = 0; q < nrhs; ++q) {
-        if (act[q] == 0.0) continue;
-        double rr = relres_of(rn2[q], fn2[q]);
-        if (rr <= tol) { act[q] = 0.0; continue; }
-        // a column whose FP64 residual has not halved in 4 folds has reached
-        // what the FP32 phase can do; the FP64 phase takes it from here
-        if (rn2[q] < 0.25 * best[q]) { best[q] = rn2[q]; since_best[q] = 0; }
-        else if (++since_best[q] > 4) { act[q] = 0.0; continue; }
-        any = true;
-      }
-      if (trace)
-        std::fprintf(stderr, "[cpm reliable] update %d it %d relres[0] %.3e fp32 |r|/|r0| %.3e\n", nupd, it,
-                     relres_of(rn2[0], fn2[0]), nupd ? std::sqrt(w->h_pinned[9] / w->h_pinned[14]) : 1.0);
-      ++nupd;
-      last_update = it;
-      if (!any || nupd > max_updates) break;
-      // the residual is replaced for columns whose x changed (accepted or
-      // restarted); a rejected column keeps its FP32 recursive residual
-      for (int q = 0; q < nrhs; ++q) drop[q] = (act[q] != 0.0 && replace[q] != 0.0) ? 1.0 : 0.0;
-      CPM_CUDA_TRY(cudaMemcpyAsync(d_rn2, rn2.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-      CPM_CUDA_TRY(cudaMemcpyAsync(d_act, drop.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-      CPM_CUDA_TRY(cudaMemcpyAsync(d_reset, reset.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-      replace_r_kernel<<<g, 256, 0, st>>>(N, c->NS, wfp32, form.shadow_mix, nrhs, ld, d_act, d_reset, w->r64, r, rh, p,
-                                          v);
-      cpm_count_launches(c, 1);
-      // the FP32 recursive residual restarts from the replaced one (which is
-      // already W r, so its plain norm is the weighted norm)
-      std::vector<double> rs2(nrhs);
-      for (int q = 0; q < nrhs; ++q) rs2[q] = (wfp32 == wrow) ? rn2[q] : -1.0;
-      CPM_CUDA_TRY(cudaMemcpyAsync(d_rn2, rs2.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-      for (int q = 0; q < nrhs; ++q) acc[q] = act[q];
-      CPM_CUDA_TRY(cudaMemcpyAsync(w->d_cols + 3 * nrhs, acc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice,
-                                   st));
-      scal_reliable_kernel<<<1, 256, 0, st>>>(w->sc, d_rn2, w->d_cols + 3 * nrhs, d_act, d_reset, nrhs);
-      cpm_count_launches(c, 1);
-      if (wfp32 != wrow) {
-        // the FP32 residual norm differs from the measured one: take it from r32
-        dots<float>(w, 1, r, r, nullptr, nullptr, nullptr, nullptr, N, st);
-        scal_setr_kernel<<<1, 256, 0, st>>>(w->sc, w->dots, d_act, nrhs);
-        cpm_count_launches(c, 1);
-      }
-      std::fill(replace.begin(), replace.end(), 1.0);
-      std::fill(reset.begin(), reset.end(), 0.0);
-      do_update = false;
-    }
-    if (it >= maxit) break;
-    int steps = std::min(check_every, maxit - it);
-    for (int k = 0; k < steps; ++k) {
-      rc = iteration<float>(c, ap32, form, m, n, x32, w, tol, 0, st);
-      if (rc) return rc;
-    }
-    CPM_CUDA_TRY(cudaGetLastError());
-    it += steps;
-    rc = read_scalars(w, st);
-    if (rc) return rc;
+  int it_total = 0, nout = 0, nrs = 0;
+  while (nout < max_outer && it_total < maxit) {
+    bool any = false;
     for (int q = 0; q < nrhs; ++q) {
-      if (act[q] == 0.0) continue;
-      const double *sq = w->h_pinned + q * NSC;
-      // recursive residual dropped by delta since the last update, or reached
-      // the tolerance: fold and replace; broke down or diverged: also restart
-      if (sq[9] <= delta * delta * sq[14] || std::sqrt(sq[9]) <= tol * std::sqrt(sq[8])) do_update = true;
-      if (sq[9] > 1e4 * sq[14]) do_update = true;  // the FP32 iteration is running away
-      if (sq[10] != 0.0 || sq[13] != 0.0 || sq[5] == 0.0) {
-        do_update = true;
-        reset[q] = 1.0;
-        ++nrestart;
-      }
+      if (!act[q]) { scale[q] = 0.0; continue; }
+      if (relres_of(rn2[q], fn2[q]) <= tol) { act[q] = 0; scale[q] = 0.0; continue; }
+      if (rn2[q] < 0.25 * best[q]) { best[q] = rn2[q]; stall[q] = 0; }
+      else if (++stall[q] >= 2) { act[q] = 0; scale[q] = 0.0; continue; }
+      scale[q] = std::sqrt(rn2[q]);
+      any = true;
     }
-    if (it - last_update >= max_between) do_update = true;
-    if (nrestart > 40) { *broke = true; break; }
-  }
-  // fold what is left where it helps
-  {
-    candidate_kernel<<<g, 256, 0, st>>>(N, nrhs, ld, x, x32, w->fs);
+    if (trace)
+      std::fprintf(stderr, "[cpm ir] outer %d it %d relres[0] %.3e worst %.3e\n", nout, it_total,
+                   relres_of(rn2[0], fn2[0]), worst_relres(rn2, fn2));
+    if (!any) break;
+    CPM_CUDA_TRY(cudaMemcpyAsync(d_scale, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+    ir_rhs_kernel<<<g, 256, 0, st>>>(N, c->NS, dS, nrhs, ld, d_scale, w->r64, w->f32);
+    CPM_CUDA_TRY(cudaMemsetAsync(w->xd, 0, sizeof(double) * (size_t)N * ld, st));
     cpm_count_launches(c, 1);
+    int it = 0, rs = 0;
+    bool broke = false;
+    rc = bicgstab<float, double>(c, ap32, form32, m, n, w->f32, w->xd, w, inner_tol,
+                                 std::min(inner_maxit, maxit - it_total), check_every, &it, &rs, &broke, st);
+    if (rc) return rc;
+    it_total += it;
+    nrs += rs;
+    // keep the correction only where the FP64 residual went down; a column
+    // whose FP32 solve made it worse is left for the FP64 finish
+    ir_candidate_kernel<<<g, 256, 0, st>>>(N, nrhs, ld, d_scale, w->xd, x, w->fs);
+    cpm_count_launches(c, 1);
+    ++nout;
     std::vector<double> rn2_prev = rn2;
     rc = residual64(c, ap64, m, n, f, w->fs, w, wrow, rn2, fn2, st);
     if (rc) return rc;
+    std::vector<double> acc(nrhs, 0.0);
     bool rejected = false;
     for (int q = 0; q < nrhs; ++q) {
-      acc[q] = (std::isfinite(rn2[q]) && rn2[q] <= rn2_prev[q]) ? 1.0 : 0.0;
-      if (acc[q] == 0.0) rejected = true;
+      if (scale[q] == 0.0) { rn2[q] = rn2_prev[q]; continue; }
+      if (std::isfinite(rn2[q]) && rn2[q] < rn2_prev[q]) {
+        acc[q] = 1.0;
+      } else {
+        rejected = true;
+        act[q] = 0;
+        rn2[q] = rn2_prev[q];
+      }
     }
-    std::vector<double> ones(nrhs, 1.0);
-    CPM_CUDA_TRY(cudaMemcpyAsync(d_act, acc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-    CPM_CUDA_TRY(cudaMemcpyAsync(d_reset, ones.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-    accept_kernel<<<g, 256, 0, st>>>(N, nrhs, ld, d_act, d_reset, w->fs, x, x32);
+    CPM_CUDA_TRY(cudaMemcpyAsync(d_scale, acc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+    accept_kernel<<<g, 256, 0, st>>>(N, nrhs, ld, d_scale, w->fs, x);
     cpm_count_launches(c, 1);
     if (rejected) {
+      // r64 must hold the residual of x for the next outer step
       rc = residual64(c, ap64, m, n, f, x, w, wrow, rn2, fn2, st);
       if (rc) return rc;
     }
   }
-  *iters = it;
-  *updates = nupd;
-  *restarts = nrestart;
+  *iters = it_total;
+  *outers = nout;
+  *restarts = nrs;
   return CPM_OK;
 }
 
 static cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const double *f, double *x, int nrhs,
                              int64_t ld, const cpm_solve_opts *o, cpm_solve_stats *stats, cudaStream_t st) {
-  cpm_solve_opts opts{1e-10, 10000, CPM_SOLVE_FP64, 0.1, 200, 16, CPM_NORM_SCALED, 1000};
+  cpm_solve_opts opts{1e-10, 10000, CPM_SOLVE_FP64, 1e-2, 200, 16, CPM_NORM_SCALED, 1000};
   if (o) opts = *o;
   if (opts.tol <= 0) opts.tol = 1e-10;
   if (opts.maxit <= 0) opts.maxit = 10000;
-  if (opts.inner_tol <= 0 || opts.inner_tol >= 1) opts.inner_tol = 0.1;
+  if (opts.inner_tol <= 0 || opts.inner_tol >= 1) opts.inner_tol = 1e-2;
   if (opts.max_refine <= 0) opts.max_refine = 200;
   if (opts.check_every <= 0) opts.check_every = 16;
   if (opts.inner_maxit <= 0) opts.inner_maxit = 1000;
@@ -772,15 +652,15 @@ static cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const
       prev_worst = worst;
     }
   } else if (opts.mode == CPM_SOLVE_FP32_IR) {
-    rc = get_work(c, w, N, nrhs, ld, sizeof(float));
-    if (rc) return rc;
     ApplyFn<float> ap32 = adjoint ? cpm_apply_transpose_scaled_T<float> : cpm_apply_scaled_T<float>;
     // the FP32 iteration always runs on the row-scaled system (its residual is
     // balanced); the requested norm decides acceptance and convergence
     KrylovForm form32{1.0, dS, 4000.0, 0.5f};
-    rc = bicgstab_reliable(c, ap64, ap32, form32, m, n, f, x, w, wrow, dS, opts.tol, opts.inner_tol, opts.inner_maxit,
-                           opts.maxit, opts.max_refine, opts.check_every, trace, &iters, &refinements, &restarts,
-                           &broke, rn2, fn2, st);
+    rc = get_work(c, w, N, nrhs, ld, sizeof(float));
+    if (rc) return rc;
+    rc = ir_restarted(c, ap64, ap32, form32, m, n, f, x, w, wrow, dS, opts.tol, opts.inner_tol, opts.inner_maxit,
+                      opts.maxit, opts.max_refine, opts.check_every, trace, &iters, &refinements, &restarts, rn2, fn2,
+                      st);
     if (rc) return rc;
     if (!(worst_relres(rn2, fn2) <= opts.tol) && iters < opts.maxit) {
       // FP64 finish from the current iterate for the columns the FP32 phase
