@@ -33,6 +33,7 @@
 #ifndef CPM_H
 #define CPM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -173,6 +174,33 @@ cpm_status cpm_rhs(cpm_ctx *ctx, const double *s_dev, const double *g_dev, const
  * Requires cpm_set_boundary (possibly with no curves).  Asynchronous. */
 cpm_status cpm_apply(cpm_ctx *ctx, double m, double n, int prec, const void *u_dev, void *v_dev, int nrhs,
                      int64_t ld, void *stream);
+
+/* cpm_apply without any allocation.  The paper has no counterpart: this is a
+ * library-level variant for callers that cannot allocate device memory at the
+ * time of the call -- for instance a host framework that has already handed all
+ * device memory to its own pool (a cudaMalloc would fail), or a latency-bound
+ * caller that must not pay the implicit device synchronisation of cudaMalloc /
+ * cudaFree.  Same arguments, layout and result as cpm_apply; the E u
+ * intermediate goes to one fixed device array of cpm_apply_noalloc_max_bytes()
+ * bytes (16 MiB) inside the library instead of the context's scratch, which
+ * cpm_apply grows on demand.
+ *  - Size limit: element size x N_S x ld must not exceed that many bytes,
+ *    otherwise CPM_ERR_CAPACITY is returned and nothing is launched.
+ *  - The array's device address is looked up (cudaGetSymbolAddress) on the
+ *    first call for each device, with that device current; make the first call
+ *    on a device before any stream capture.  A failed lookup returns CPM_ERR_CUDA.
+ *  - Nothing needs to start at zero: every element that is read was written
+ *    earlier in the same call.
+ *  - The array is shared by all contexts and streams on a device: calls that
+ *    overlap in time on one device race on it and must be serialised by the
+ *    caller.
+ * Errors: ARG (null pointer, bad nrhs/ld, unknown prec), STATE (no boundary
+ * set), CAPACITY, CUDA.  Asynchronous. */
+cpm_status cpm_apply_noalloc(cpm_ctx *ctx, double m, double n, int prec, const void *u_dev, void *v_dev, int nrhs,
+                             int64_t ld, void *stream);
+
+/* Size in bytes of cpm_apply_noalloc's fixed intermediate array. */
+size_t cpm_apply_noalloc_max_bytes(void);
 
 /* v = A^T u (the transposed product, by a cell-bucketed gather: no atomics). */
 cpm_status cpm_apply_transpose(cpm_ctx *ctx, double m, double n, int prec, const void *u_dev, void *v_dev, int nrhs,

@@ -22,7 +22,8 @@ NORM_SCALED, NORM_PLAIN = 0, 1
 # every entry point that include/cpm.h declares
 EXPORTS = ["cpm_band_build", "cpm_band_info", "cpm_export_band", "cpm_set_boundary", "cpm_export_boundary",
            "cpm_rhs", "cpm_apply", "cpm_apply_transpose", "cpm_extend", "cpm_solve", "cpm_solve_adjoint",
-           "cpm_boundary_grad", "cpm_destroy", "cpm_status_str", "cpm_diagnostics", "cpm_profile"]
+           "cpm_boundary_grad", "cpm_destroy", "cpm_status_str", "cpm_diagnostics", "cpm_profile",
+           "cpm_apply_noalloc", "cpm_apply_noalloc_max_bytes"]
 
 
 class ShapeDesc(ctypes.Structure):
@@ -70,6 +71,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.cpm_rhs.argtypes = [P, P, P, P, P, i, i64, P]
     L.cpm_apply.argtypes = [P, d, d, i, P, P, i, i64, P]
     L.cpm_apply_transpose.argtypes = [P, d, d, i, P, P, i, i64, P]
+    L.cpm_apply_noalloc.argtypes = [P, d, d, i, P, P, i, i64, P]
+    L.cpm_apply_noalloc_max_bytes.argtypes = []
+    L.cpm_apply_noalloc_max_bytes.restype = ctypes.c_size_t
     L.cpm_extend.argtypes = [P, P, P, i, i64, P]
     L.cpm_solve.argtypes = [P, d, d, P, P, i, i64, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), P]
     L.cpm_solve_adjoint.argtypes = [P, d, d, P, P, i, i64, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), P]
@@ -81,7 +85,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.cpm_diagnostics.argtypes = [P, pi64, pi64]
     L.cpm_profile.argtypes = [P, i, ctypes.POINTER(d), pi64, pi64, pi64]
     for name in EXPORTS:
-        if name not in ("cpm_destroy", "cpm_status_str"):
+        if name not in ("cpm_destroy", "cpm_status_str", "cpm_apply_noalloc_max_bytes"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

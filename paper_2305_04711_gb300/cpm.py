@@ -184,6 +184,15 @@ class Band:
                 "cpm_apply_transpose" if transpose else "cpm_apply")
         return v
 
+    def apply_noalloc(self, m: float, n: float, u: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
+        """cpm_apply_noalloc: the product with the library's fixed intermediate
+        array (no allocation inside the call; `out` is the caller's)."""
+        nrhs, ld = _layout(u, self.N)
+        prec = {torch.float64: L.PREC_FP64, torch.float32: L.PREC_FP32}[u.dtype]
+        L.check(self._lib.cpm_apply_noalloc(self._h, float(m), float(n), prec, _ptr(u), _ptr(out), nrhs, ld,
+                                            _stream()), "cpm_apply_noalloc")
+        return out
+
     def extend(self, u: torch.Tensor) -> torch.Tensor:
         nrhs, ld = _layout(u, self.N)
         a = torch.empty((self.NS,) if nrhs == 1 else (self.NS, nrhs), dtype=torch.float64, device="cuda")

@@ -150,6 +150,19 @@ cpm_status cpm_apply(cpm_ctx *c, double m, double n, int prec, const void *u, vo
   return CPM_ERR_ARG;
 }
 
+cpm_status cpm_apply_noalloc(cpm_ctx *c, double m, double n, int prec, const void *u, void *v, int nrhs,
+                             int64_t ld, void *stream) {
+  if (!c || !u || !v || bad_batch(nrhs, ld)) return CPM_ERR_ARG;
+  if (!c->boundary_set) return CPM_ERR_STATE;
+  if (prec == CPM_PREC_FP64)
+    return cpm_apply_noalloc_T<double>(c, m, n, (const double *)u, (double *)v, nrhs, ld, as_stream(stream));
+  if (prec == CPM_PREC_FP32)
+    return cpm_apply_noalloc_T<float>(c, m, n, (const float *)u, (float *)v, nrhs, ld, as_stream(stream));
+  return CPM_ERR_ARG;
+}
+
+size_t cpm_apply_noalloc_max_bytes(void) { return cpm_noalloc_scratch_bytes(); }
+
 cpm_status cpm_apply_transpose(cpm_ctx *c, double m, double n, int prec, const void *u, void *v, int nrhs, int64_t ld,
                                void *stream) {
   if (!c || !u || !v || bad_batch(nrhs, ld)) return CPM_ERR_ARG;

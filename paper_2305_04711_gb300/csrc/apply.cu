@@ -14,8 +14,10 @@
 //            v_alpha = sum_beta B_alpha,beta u_beta                   (BC rows)
 // where a neighbour flipped to a BC DOF reads u of that DOF (E rows of BC DOFs
 // are the identity).
-#include "cpm_internal.cuh"
+#include <mutex>
+
 #include "apply.cuh"
+#include "cpm_internal.cuh"
 
 namespace {
 
@@ -530,3 +532,66 @@ cpm_status cpm_internal_boundary_grad(cpm_ctx *c, const double *lam, double *out
   CPM_CUDA_TRY(cudaStreamSynchronize(st));
   return CPM_OK;
 }
+
+// ---- operator product with a static scratch (no allocation) -----------------
+// The E u intermediate lives in a fixed module array instead of the context's
+// lazily grown scratch, so this path calls no allocator.  Nothing in the array
+// has to start at zero: every element the combine reads was written earlier in
+// the same call.  One array per device serves every context and stream, so
+// calls that overlap in time on one device race on it.
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// device address of the array for the current device, looked up on the first
+// call for that device
+cpm_status noalloc_scratch(void **out) {
+  int dev = -1;
+  CPM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return CPM_ERR_CAPACITY;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cpm_internal_cuda_err(e);
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CPM_OK;
+}
+}  // namespace
+
+size_t cpm_noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
+
+template <typename T>
+cpm_status cpm_apply_noalloc_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld,
+                               cudaStream_t st) {
+  if (sizeof(T) * (size_t)c->NS * (size_t)ld > kNoAllocScratchBytes) return CPM_ERR_CAPACITY;
+  void *p = nullptr;
+  cpm_status rc = noalloc_scratch(&p);
+  if (rc) return rc;
+  T *a = reinterpret_cast<T *>(p);
+  ApplyArgs<T> A = cpm_apply_args<T>(c);
+  const bool diff = (sizeof(T) == 4);
+  const bool aligned2 = (ld % 2 == 0) && ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v) |
+                                           reinterpret_cast<uintptr_t>(a)) % (2 * sizeof(T)) == 0);
+  int launched = 2;
+  if (nrhs > 32 && nrhs <= 64 && nrhs % 2 == 0 && aligned2)
+    launched = launch_batched<T, 2>(c, A, (T)m, (T)n, T(1), u, a, v, nrhs, ld, st, diff);
+  else if (nrhs >= 16 && nrhs <= 32)
+    launched = launch_batched<T, 1>(c, A, (T)m, (T)n, T(1), u, a, v, nrhs, ld, st, diff);
+  else {
+    cpm_launch_gather<T>(A, u, a, nrhs, ld, st, diff);
+    cpm_launch_combine<T>(A, (T)m, (T)n, T(1), u, a, v, nrhs, ld, st, diff);
+  }
+  cpm_count_launches(c, launched);
+  CPM_CUDA_TRY(cudaGetLastError());
+  return CPM_OK;
+}
+template cpm_status cpm_apply_noalloc_T<double>(cpm_ctx *, double, double, const double *, double *, int, int64_t,
+                                                cudaStream_t);
+template cpm_status cpm_apply_noalloc_T<float>(cpm_ctx *, double, double, const float *, float *, int, int64_t,
+                                               cudaStream_t);

@@ -35,6 +35,11 @@ cpm_status cpm_apply_scaled_T(cpm_ctx *c, double m, double n, double rowscale, c
 template <typename T>
 cpm_status cpm_apply_transpose_scaled_T(cpm_ctx *c, double m, double n, double rowscale, const T *u, T *v, int nrhs,
                                         int64_t ld, cudaStream_t st);
+// the product with the intermediate in a fixed module array (no allocation)
+template <typename T>
+cpm_status cpm_apply_noalloc_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld,
+                               cudaStream_t st);
+size_t cpm_noalloc_scratch_bytes();
 template <typename T>
 cpm_status cpm_apply_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld, cudaStream_t st);
 template <typename T>
