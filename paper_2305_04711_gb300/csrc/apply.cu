@@ -46,11 +46,7 @@ __device__ __forceinline__ T line4(const T *u, int64_t ld, int r, int32_t s0, in
 template <typename T, bool DIFF>
 __global__ void __launch_bounds__(256) gather_kernel(ApplyArgs<T> A, const T *__restrict__ u, T *__restrict__ a,
                                                      int nrhs, int64_t ld) {
-  const int64_t total = A.v.NS * (int64_t)nrhs;
-  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < total;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = tid / nrhs;
-    int r = (int)(tid - i * nrhs);
+  CPM_ROWS_COLS_LOOP(A.v.NS, nrhs, i, r) {
     uint32_t rb = __ldg(A.rbase + i);
     T acc = T(0);
     const T ui = DIFF ? __ldg(u + i * ld + r) : T(0);
@@ -99,14 +95,10 @@ __global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, 
                                                       const T *__restrict__ a, T *__restrict__ v, int nrhs,
                                                       int64_t ld) {
   const int64_t NS = A.v.NS, N = NS + A.v.NC;
-  const int64_t total = N * (int64_t)nrhs;
   const T inv_h2 = T(A.v.inv_h * A.v.inv_h);
   const T diag = m + n * T(-2.0 * A.v.dim * A.v.inv_h * A.v.inv_h);
   const int nfd = 2 * A.v.dim;
-  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < total;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = tid / nrhs;
-    int r = (int)(tid - i * nrhs);
+  CPM_ROWS_COLS_LOOP(N, nrhs, i, r) {
     if (i < NS) {
       uint32_t rb = __ldg(A.rbase + i);
       const T ui = __ldg(u + i * ld + r);
@@ -289,11 +281,8 @@ static int launch_batched(const cpm_ctx *c, const ApplyArgs<T> &A, T m, T n, T r
 __global__ void rhs_kernel(BandView v, const CurveDev *curves, const int32_t *bc_curve, const int32_t *side,
                            const double *param, const double *s, const double *g, const double *samples, double *f,
                            int nrhs, int64_t ld) {
-  const int64_t N = v.NS + v.NC, total = N * (int64_t)nrhs;
-  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < total;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = tid / nrhs;
-    int r = (int)(tid - i * nrhs);
+  const int64_t N = v.NS + v.NC;
+  CPM_ROWS_COLS_LOOP(N, nrhs, i, r) {
     if (i < v.NS) {
       f[i * ld + r] = s ? s[i * ld + r] : 0.0;
       continue;

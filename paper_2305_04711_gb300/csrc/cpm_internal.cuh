@@ -194,6 +194,16 @@ cpm_status cpm_build_transpose(cpm_ctx *c);
 cpm_status cpm_build_cells(cpm_ctx *c);
 void cpm_free_cells(cpm_ctx *c);
 
+// element loop over the [N][nrhs] block of a [N][ld] array without a division
+// per element: a block of B threads takes B / nrhs rows at a time, thread t
+// column t % nrhs (nrhs <= B)
+#define CPM_ROWS_COLS_LOOP(N, nrhs, i, c)                                                     \
+  const int c = (int)(threadIdx.x % (unsigned)(nrhs));                                         \
+  const int rows_per_ = (int)(blockDim.x / (unsigned)(nrhs));                                  \
+  if ((int)(threadIdx.x / (unsigned)(nrhs)) >= rows_per_) return;                              \
+  for (int64_t i = blockIdx.x * (int64_t)rows_per_ + threadIdx.x / (unsigned)(nrhs); i < (N); \
+       i += (int64_t)gridDim.x * rows_per_)
+
 static inline unsigned cpm_grid(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   if (g < 1) g = 1;

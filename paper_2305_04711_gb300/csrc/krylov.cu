@@ -57,12 +57,20 @@ __global__ void __launch_bounds__(RED_THREADS) dots_kernel(const T *__restrict__
   if (sub < rows_per) {
     int64_t chunk = (N + gridDim.x - 1) / gridDim.x;
     int64_t lo = blockIdx.x * chunk, hi = lo + chunk < N ? lo + chunk : N;
-    for (int64_t i = lo + sub; i < hi; i += rows_per) {
-      int64_t o = i * ld + r;
-      double wi = (i < NS) ? wpde : 1.0;
-      acc0 += wi * ((double)a0[o] * (double)b0[o]);
-      if (nq > 1) acc1 += wi * ((double)a1[o] * (double)b1[o]);
-      if (nq > 2) acc2 += wi * ((double)a2[o] * (double)b2[o]);
+    // runs of 16 products are summed in T, the runs in FP64 (for FP32 vectors
+    // this keeps the FP64 pipe, 1/64 of the FP32 rate here, off the hot loop)
+    for (int64_t i = lo + sub; i < hi;) {
+      T c0 = T(0), c1 = T(0), c2 = T(0);
+      for (int k = 0; k < 16 && i < hi; ++k, i += rows_per) {
+        const int64_t o = i * ld + r;
+        const T wi = (i < NS) ? T(wpde) : T(1);
+        c0 += wi * (a0[o] * b0[o]);
+        if (nq > 1) c1 += wi * (a1[o] * b1[o]);
+        if (nq > 2) c2 += wi * (a2[o] * b2[o]);
+      }
+      acc0 += (double)c0;
+      acc1 += (double)c1;
+      acc2 += (double)c2;
     }
   }
   sh[0][t] = acc0; sh[1][t] = acc1; sh[2][t] = acc2;
@@ -183,10 +191,7 @@ __device__ __forceinline__ float shadow_weight(int64_t i, int c, float mix) {
 template <typename T>
 __global__ void upd_p_kernel(const double *sc, int64_t N, int64_t NS, int nrhs, int64_t ld, T dS, float mix,
                              const T *r, T *rh, T *p, const T *v, T *ph) {
-  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = tid / nrhs;
-    int c = (int)(tid - i * nrhs);
+  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
     const double *s = sc + c * NSC;
     if (s[5] == 0.0) continue;
     int64_t o = i * ld + c;
@@ -198,7 +203,7 @@ __global__ void upd_p_kernel(const double *sc, int64_t N, int64_t NS, int nrhs, 
       pv = r[o] + T(s[4]) * (p[o] - T(s[2]) * v[o]);
     }
     p[o] = pv;
-    ph[o] = dinv_of<T>(i, NS, dS) * pv;
+    if (ph != p) ph[o] = dinv_of<T>(i, NS, dS) * pv;
   }
 }
 
@@ -206,16 +211,13 @@ __global__ void upd_p_kernel(const double *sc, int64_t N, int64_t NS, int nrhs, 
 template <typename T>
 __global__ void upd_s_kernel(const double *sc, int64_t N, int64_t NS, int nrhs, int64_t ld, T dS, const T *r,
                              const T *v, T *s_, T *sh) {
-  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = tid / nrhs;
-    int c = (int)(tid - i * nrhs);
+  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
     const double *s = sc + c * NSC;
     if (s[5] == 0.0) continue;
     int64_t o = i * ld + c;
     T sv = r[o] - T(s[1]) * v[o];
     s_[o] = sv;
-    sh[o] = dinv_of<T>(i, NS, dS) * sv;
+    if (sh != s_) sh[o] = dinv_of<T>(i, NS, dS) * sv;
   }
 }
 
@@ -225,10 +227,7 @@ __global__ void upd_s_kernel(const double *sc, int64_t N, int64_t NS, int nrhs, 
 template <typename T, typename TX>
 __global__ void upd_xr_kernel(const double *sc, int64_t N, int nrhs, int64_t ld, TX *x, T *r, const T *ph,
                               const T *sh, const T *s_, const T *t) {
-  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = tid / nrhs;
-    int c = (int)(tid - i * nrhs);
+  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
     const double *s = sc + c * NSC;
     if (s[5] == 0.0) continue;
     int64_t o = i * ld + c;
@@ -241,10 +240,7 @@ __global__ void upd_xr_kernel(const double *sc, int64_t N, int nrhs, int64_t ld,
 // r = f - r (r holds A x);  rhat = r;  p = v = 0
 template <typename T>
 __global__ void init_r_kernel(int64_t N, int nrhs, int64_t ld, const T *f, T *r, T *rh, T *p, T *v) {
-  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = tid / nrhs;
-    int c = (int)(tid - i * nrhs);
+  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
     int64_t o = i * ld + c;
     T rv = f[o] - r[o];
     r[o] = rv;
@@ -257,10 +253,7 @@ __global__ void init_r_kernel(int64_t N, int nrhs, int64_t ld, const T *f, T *r,
 // ---- FP64 pieces ------------------------------------------------------------
 // r = f - r (r holds A x)
 __global__ void residual64_kernel(int64_t N, int nrhs, int64_t ld, const double *f, double *r) {
-  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = tid / nrhs;
-    int c = (int)(tid - i * nrhs);
+  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
     int64_t o = i * ld + c;
     r[o] = f[o] - r[o];
   }
@@ -269,10 +262,7 @@ __global__ void residual64_kernel(int64_t N, int nrhs, int64_t ld, const double 
 // out = W f (PDE rows scaled by dS)
 __global__ void scale_rows64_kernel(int64_t N, int64_t NS, int nrhs, int64_t ld, double dS, const double *f,
                                     double *out) {
-  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = tid / nrhs;
-    int c = (int)(tid - i * nrhs);
+  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
     int64_t o = i * ld + c;
     out[o] = (i < NS) ? dS * f[o] : f[o];
   }
@@ -280,10 +270,7 @@ __global__ void scale_rows64_kernel(int64_t N, int64_t NS, int nrhs, int64_t ld,
 
 // columns with acc != 0 take the candidate
 __global__ void accept_kernel(int64_t N, int nrhs, int64_t ld, const double *acc, const double *xc, double *x) {
-  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = tid / nrhs;
-    int c = (int)(tid - i * nrhs);
+  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
     int64_t o = i * ld + c;
     if (acc[c] != 0.0) x[o] = xc[o];
   }
@@ -293,10 +280,7 @@ __global__ void accept_kernel(int64_t N, int nrhs, int64_t ld, const double *acc
 // (scale 0: inactive column, zero right-hand side)
 __global__ void ir_rhs_kernel(int64_t N, int64_t NS, double wrow, int nrhs, int64_t ld, const double *scale,
                               const double *r64, float *f32) {
-  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = tid / nrhs;
-    int c = (int)(tid - i * nrhs);
+  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
     int64_t o = i * ld + c;
     double sc = scale[c];
     f32[o] = (sc > 0.0) ? (float)(((i < NS) ? wrow : 1.0) * r64[o] / sc) : 0.0f;
@@ -306,10 +290,7 @@ __global__ void ir_rhs_kernel(int64_t N, int64_t NS, double wrow, int nrhs, int6
 // candidate xc = x + scale * d (FP64 accumulation of the FP32 correction)
 __global__ void ir_candidate_kernel(int64_t N, int nrhs, int64_t ld, const double *scale, const double *d,
                                     const double *x, double *xc) {
-  for (int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tid < N * nrhs;
-       tid += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = tid / nrhs;
-    int c = (int)(tid - i * nrhs);
+  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
     int64_t o = i * ld + c;
     double sc = scale[c];
     xc[o] = (sc > 0.0) ? x[o] + sc * d[o] : x[o];
@@ -408,6 +389,11 @@ static cpm_status iteration(cpm_ctx *c, ApplyFn<T> apply, const KrylovForm &form
   T *r = (T *)w->vec[0], *rh = (T *)w->vec[1], *p = (T *)w->vec[2], *v = (T *)w->vec[3], *s = (T *)w->vec[4],
     *t = (T *)w->vec[5], *ph = (T *)w->vec[6], *sh = (T *)w->vec[7];
   const T dS = T(form.right);
+  // without a right preconditioner D p = p and D s = s: no copies
+  if (form.right == 1.0) {
+    ph = p;
+    sh = s;
+  }
   const unsigned g = cpm_grid(N * nrhs, 256);
   dots<T>(w, 2, rh, r, rh, rh, nullptr, nullptr, N, st);
   scal_rho_kernel<<<1, 256, 0, st>>>(w->sc, w->dots, nrhs);
