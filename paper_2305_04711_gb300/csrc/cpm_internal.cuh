@@ -148,10 +148,11 @@ struct cpm_ctx {
   float *d_corr_w32 = nullptr;      // [ncorr_ent]
   // transposed structure (adjoint)
   bool transpose_ready = false;
-  int64_t nT = 0;                   // explicit transposed entries (special E/FD rows, BC rows)
+  int64_t nT = 0;                   // entries of the per-column remainder lists
+  int32_t *d_cellid = nullptr;      // [nb*512] cell index of a packed base location, -1 if none
   int32_t *d_T_ptr = nullptr;       // [N+1] CSR over columns
-  int32_t *d_T_row = nullptr;       // [nT] source row
-  int32_t *d_T_kind = nullptr;      // [nT] 0: E entry of special row, 1: FD entry of special row, 2: BC row entry
+  int32_t *d_T_row = nullptr;       // [nT] source DOF
+  int32_t *d_T_kind = nullptr;      // [nT] 0: flipped FD entry, 1: flipped E entry, 2: BC-row entry
   double *d_T_val = nullptr;        // [nT]
   float *d_T_val32 = nullptr;       // [nT]
   // scratch
