@@ -285,6 +285,89 @@ class Oracle:
         _check(lib().orc_extend(self._h, _ptr(u), _ptr(a)))
         return a
 
+    def fd_neighbours(self) -> np.ndarray:
+        """[NS, 6] FD neighbour columns of each PDE row in the order x-, x+, y-,
+        y+, z-, z+ as the Laplacian rows use them (Eq. 2 with the flips of
+        Eq. 11): the PDE DOF at x_i +- h e_d, or its BC twin where the row's
+        stencil was flipped to it; -1 where the node is not in the band."""
+        if getattr(self, "_nb", None) is not None:
+            return self._nb
+        ijk = self.ijk.astype(np.int64)
+        lo = ijk.min(axis=0) - 2
+        ext = ijk.max(axis=0) - lo + 3
+        def key(p):
+            q = p - lo
+            return (q[:, 2] * ext[1] + q[:, 1]) * ext[0] + q[:, 0]
+        keys = key(ijk)
+        order = np.argsort(keys)
+        skeys = keys[order]
+        # flipped FD entries: Loff entries (i, alpha >= NS) replace node twin[alpha]
+        Lo = self.Loff.tocoo()
+        sel = Lo.col >= self.NS
+        flip = {(int(i), int(self.twin[c - self.NS])): int(c) for i, c in zip(Lo.row[sel], Lo.col[sel])}
+        out = -np.ones((self.NS, 6), dtype=np.int64)
+        for d in range(self.dim):
+            for sg, slot in ((-1, 2 * d), (1, 2 * d + 1)):
+                q = ijk.copy()
+                q[:, d] += sg
+                kq = key(q)
+                pos = np.clip(np.searchsorted(skeys, kq), 0, len(skeys) - 1)
+                found = skeys[pos] == kq
+                out[:, slot] = np.where(found, order[pos], -1)
+        for (i, j), c in flip.items():
+            row = out[i]
+            row[row == j] = c
+        self._nb = out
+        return out
+
+    def _central(self, at: np.ndarray, a: np.ndarray, nb: np.ndarray, d: int) -> np.ndarray:
+        vp = np.where(nb[:, 2 * d + 1] >= 0, at[np.maximum(nb[:, 2 * d + 1], 0)], a)
+        vm = np.where(nb[:, 2 * d] >= 0, at[np.maximum(nb[:, 2 * d], 0)], a)
+        return (vp - vm) / (2.0 * self.h)
+
+    def surface_gradient(self, u: np.ndarray, normalize: bool = False) -> np.ndarray:
+        """Central differences of the CP extension (Sec. 7.2, step 2): at PDE row
+        i, g_d = (a(n+) - a(n-)) / 2h over its FD neighbours, with a = E u on PDE
+        DOFs and u itself on BC DOFs; a missing neighbour takes a_i.  normalize:
+        X = -g / |g| (0 where g = 0).  BC DOFs take their twin node's value.
+        Returns [N, 3]."""
+        u = np.asarray(u, dtype=np.float64)
+        a = self.extend(u)
+        at = np.concatenate([a, u[self.NS:]])
+        nb = self.fd_neighbours()
+        g = np.zeros((self.NS, 3))
+        for d in range(self.dim):
+            g[:, d] = self._central(at, a, nb, d)
+        if normalize:
+            nrm = np.sqrt(np.sum(g * g, axis=1))
+            g = np.where(nrm[:, None] > 0, -g / np.where(nrm > 0, nrm, 1.0)[:, None], 0.0)
+        return np.concatenate([g, g[self.twin]]) if self.NC else g
+
+    def surface_divergence(self, X: np.ndarray) -> np.ndarray:
+        """Central-difference divergence of the CP extension of the field X
+        ([N, 3]) at the PDE rows (the right-hand side of Sec. 7.2, step 3)."""
+        X = np.asarray(X, dtype=np.float64)
+        nb = self.fd_neighbours()
+        b = np.zeros(self.NS)
+        for d in range(self.dim):
+            a = self.extend(np.ascontiguousarray(X[:, d]))
+            at = np.concatenate([a, X[self.NS:, d]])
+            b += self._central(at, a, nb, d)
+        return b
+
+    def heat_geodesic(self, dt: float, extra: int = 0) -> np.ndarray:
+        """The heat method of Sec. 7.2 with the curves as the distance source:
+        (1) one implicit Euler step (I - dt M) v = 0 off C, v = 1 on C;
+        (2) X = -grad v / |grad v|; (3) M phi = div X with phi = 0 on C.
+        `extra` repeats (2)-(3) with X = grad phi / |grad phi|.  Direct solves."""
+        v = self.solve_direct(1.0, -dt, self.rhs(None, np.ones(self.NC)))
+        X = self.surface_gradient(v, normalize=True)
+        for _ in range(extra + 1):
+            b = self.surface_divergence(X)
+            phi = self.solve_direct(0.0, 1.0, self.rhs(b, np.zeros(self.NC)))
+            X = self.surface_gradient(-phi, normalize=True)
+        return phi
+
     def precond(self, m: float, n: float) -> np.ndarray:
         d = np.ones(self.N)
         d[:self.NS] = 1.0 / (m + n * self.diagL())

@@ -507,10 +507,11 @@ static double worst_relres(const std::vector<double> &rn2, const std::vector<dou
 // |W r| d to x in FP64.  Every inner solve starts a fresh Krylov space, so a
 // loss of accuracy in one FP32 solve does not carry into the next.  A column
 // whose FP64 residual fails to halve over two outer steps is left for the
-// FP64 finish.
+// FP64 finish.  rhs_w weights the PDE rows of the inner right-hand side: the
+// scaling of the left-scaled form, or 1 for a right-preconditioned inner form.
 static cpm_status ir_restarted(cpm_ctx *c, ApplyFn<double> ap64, ApplyFn<float> ap32, const KrylovForm &form32,
-                               double m, double n, const double *f, double *x, SolveWork *w, double wrow, double dS,
-                               double tol, double inner_tol, int inner_maxit, int maxit, int max_outer,
+                               double m, double n, const double *f, double *x, SolveWork *w, double wrow,
+                               double rhs_w, double tol, double inner_tol, int inner_maxit, int maxit, int max_outer,
                                int check_every, bool trace, int *iters, int *outers, int *restarts,
                                std::vector<double> &rn2, std::vector<double> &fn2, cudaStream_t st) {
   const int64_t N = c->NS + c->NC;
@@ -539,7 +540,7 @@ static cpm_status ir_restarted(cpm_ctx *c, ApplyFn<double> ap64, ApplyFn<float> 
                    relres_of(rn2[0], fn2[0]), worst_relres(rn2, fn2));
     if (!any) break;
     CPM_CUDA_TRY(cudaMemcpyAsync(d_scale, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-    ir_rhs_kernel<<<g, 256, 0, st>>>(N, c->NS, dS, nrhs, ld, d_scale, w->r64, w->f32);
+    ir_rhs_kernel<<<g, 256, 0, st>>>(N, c->NS, rhs_w, nrhs, ld, d_scale, w->r64, w->f32);
     CPM_CUDA_TRY(cudaMemsetAsync(w->xd, 0, sizeof(double) * (size_t)N * ld, st));
     cpm_count_launches(c, 1);
     int it = 0, rs = 0;
@@ -608,13 +609,17 @@ static cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const
   std::vector<double> rn2, fn2;
   ApplyFn<double> ap64 = adjoint ? cpm_apply_transpose_scaled_T<double> : cpm_apply_scaled_T<double>;
   // scaled: BiCGSTAB on (W A) x = W f, so its recursive residual is the
-  // measured one; plain: the paper's right-preconditioned form
-  KrylovForm form = scaled ? KrylovForm{1.0, dS, 4000.0, 0.0f} : KrylovForm{dS, 1.0, 4000.0, 0.0f};
+  // measured one; plain: the paper's right-preconditioned form.  The adjoint
+  // always iterates right-preconditioned, A^T W mu = g with lambda = W mu: this
+  // is the transpose of the row-scaled forward system, whereas scaling the rows
+  // of A^T leaves the BC rows with O(1/h^2) couplings and BiCGSTAB breaks down.
+  const bool left = scaled && !adjoint;
+  KrylovForm form = left ? KrylovForm{1.0, dS, 4000.0, 0.0f} : KrylovForm{dS, 1.0, 4000.0, 0.0f};
   if (opts.mode == CPM_SOLVE_FP64) {
     rc = get_work(c, w, N, nrhs, ld, sizeof(double));
     if (rc) return rc;
     const double *rhs = f;
-    if (scaled) {
+    if (left) {
       scale_rows64_kernel<<<cpm_grid(N * nrhs, 256), 256, 0, st>>>(N, c->NS, nrhs, ld, dS, f, w->fs);
       cpm_count_launches(c, 1);
       rhs = w->fs;
@@ -641,10 +646,10 @@ static cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const
     ApplyFn<float> ap32 = adjoint ? cpm_apply_transpose_scaled_T<float> : cpm_apply_scaled_T<float>;
     // the FP32 iteration always runs on the row-scaled system (its residual is
     // balanced); the requested norm decides acceptance and convergence
-    KrylovForm form32{1.0, dS, 4000.0, 0.5f};
+    KrylovForm form32 = adjoint ? KrylovForm{dS, 1.0, 4000.0, 0.5f} : KrylovForm{1.0, dS, 4000.0, 0.5f};
     rc = get_work(c, w, N, nrhs, ld, sizeof(float));
     if (rc) return rc;
-    rc = ir_restarted(c, ap64, ap32, form32, m, n, f, x, w, wrow, dS, opts.tol, opts.inner_tol, opts.inner_maxit,
+    rc = ir_restarted(c, ap64, ap32, form32, m, n, f, x, w, wrow, adjoint ? 1.0 : dS, opts.tol, opts.inner_tol, opts.inner_maxit,
                       opts.maxit, opts.max_refine, opts.check_every, trace, &iters, &refinements, &restarts, rn2, fn2,
                       st);
     if (rc) return rc;
@@ -656,7 +661,7 @@ static cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const
       rc = get_work(c, w64, N, nrhs, ld, sizeof(double));
       if (rc) return rc;
       const double *rhs = f;
-      if (scaled) {
+      if (left) {
         scale_rows64_kernel<<<cpm_grid(N * nrhs, 256), 256, 0, st>>>(N, c->NS, nrhs, ld, dS, f, w64->fs);
         cpm_count_launches(c, 1);
         rhs = w64->fs;
