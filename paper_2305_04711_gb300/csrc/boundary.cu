@@ -278,7 +278,7 @@ void cpm_free_boundary(cpm_ctx *c) {
   cudaFree(c->d_bc_val); cudaFree(c->d_bc_val32); cudaFree(c->d_spec_row); cudaFree(c->d_spec_of);
   cudaFree(c->d_spec_ecol); cudaFree(c->d_spec_ew); cudaFree(c->d_spec_ew32); cudaFree(c->d_spec_fcol);
   cpm_free_cells(c);
-  cudaFree(c->d_T_ptr); cudaFree(c->d_T_row); cudaFree(c->d_cellid);
+  cudaFree(c->d_T_ptr); cudaFree(c->d_T_row); cudaFree(c->d_cellid); cudaFree(c->d_w1d64); cudaFree(c->d_w1d32);
   cudaFree(c->d_T_kind); cudaFree(c->d_T_val); cudaFree(c->d_T_val32);
   delete[] c->h_curves;
   c->h_curves = nullptr;
@@ -286,7 +286,7 @@ void cpm_free_boundary(cpm_ctx *c) {
   c->d_cpc = nullptr; c->d_side = nullptr; c->d_param = nullptr; c->d_bc_cnt = nullptr; c->d_bc_col = nullptr;
   c->d_bc_val = nullptr; c->d_bc_val32 = nullptr; c->d_spec_row = nullptr; c->d_spec_of = nullptr;
   c->d_spec_ecol = nullptr; c->d_spec_ew = nullptr; c->d_spec_ew32 = nullptr; c->d_spec_fcol = nullptr;
-  c->d_T_ptr = nullptr; c->d_T_row = nullptr; c->d_cellid = nullptr; c->nT = 0;
+  c->d_T_ptr = nullptr; c->d_T_row = nullptr; c->d_cellid = nullptr; c->nT = 0; c->d_w1d64 = nullptr; c->d_w1d32 = nullptr;
   c->d_T_kind = nullptr; c->d_T_val = nullptr; c->d_T_val32 = nullptr;
   c->transpose_ready = false;
   c->boundary_set = false;

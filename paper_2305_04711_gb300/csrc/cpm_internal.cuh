@@ -150,6 +150,8 @@ struct cpm_ctx {
   bool transpose_ready = false;
   int64_t nT = 0;                   // entries of the per-column remainder lists
   int32_t *d_cellid = nullptr;      // [nb*512] cell index of a packed base location, -1 if none
+  double *d_w1d64 = nullptr;        // [NS][12] per-axis Lagrange factors (transposed gather)
+  float *d_w1d32 = nullptr;         // [NS][12]
   int32_t *d_T_ptr = nullptr;       // [N+1] CSR over columns
   int32_t *d_T_row = nullptr;       // [nT] source DOF
   int32_t *d_T_kind = nullptr;      // [nT] 0: flipped FD entry, 1: flipped E entry, 2: BC-row entry

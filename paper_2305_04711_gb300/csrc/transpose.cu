@@ -33,12 +33,18 @@ __device__ __forceinline__ int64_t loc_of(const BandView &v, int32_t b, int lx, 
   return ((int64_t)b << 9) | (int64_t)((lz & 7) * 64 + (ly & 7) * 8 + (lx & 7));
 }
 
-// Lagrange basis polynomial k of the 4-point stencil at t (nodes 0..3)
-template <typename T>
-__device__ __forceinline__ T lagrange_k(T t, int k) {
-  T w[4];
-  cpm_lagrange4<T>(t, w);
-  return (k == 0) ? w[0] : (k == 1) ? w[1] : (k == 2) ? w[2] : w[3];
+// per PDE row its 1-D Lagrange factors along each axis ([NS][12]: x, y, z)
+__global__ void w1d_kernel(int64_t NS, int dim, const double *t64, double *w64, float *w32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < NS; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int a = 0; a < 3; ++a) {
+      double w[4] = {1.0, 0.0, 0.0, 0.0};
+      if (a < dim) cpm_lagrange4<double>(t64[3 * i + a], w);
+      for (int k = 0; k < 4; ++k) {
+        w64[i * 12 + 4 * a + k] = w[k];
+        w32[i * 12 + 4 * a + k] = (float)w[k];
+      }
+    }
+  }
 }
 
 __global__ void cellid_kernel(const uint32_t *cell_key, int64_t ncells, int32_t *cellid) {
@@ -116,7 +122,7 @@ template <typename T>
 struct TArgs {
   BandView v;
   const uint32_t *rself;
-  const T *t;
+  const T *w1d;  // [NS][12] per-axis Lagrange factors
   const int32_t *nbr8;
   const int32_t *cellid;
   const int32_t *cell_start;
@@ -174,8 +180,8 @@ __global__ void __launch_bounds__(256) ty_kernel(TArgs<T> A, T dg, T s, T rowsca
             const int32_t q1 = __ldg(A.cell_start + cell + 1);
             for (int32_t q = __ldg(A.cell_start + cell); q < q1; ++q) {
               const int64_t row = __ldg(A.cell_rows + q);
-              T w = lagrange_k<T>(__ldg(A.t + 3 * row), cx) * lagrange_k<T>(__ldg(A.t + 3 * row + 1), cy);
-              if (A.v.dim == 3) w *= lagrange_k<T>(__ldg(A.t + 3 * row + 2), cz);
+              const T *wr = A.w1d + row * 12;
+              const T w = __ldg(wr + cx) * __ldg(wr + 4 + cy) * __ldg(wr + 8 + cz);
               acc += w * __ldg(bv + row * ld + r);
             }
           }
@@ -197,7 +203,8 @@ __global__ void __launch_bounds__(256) ty_kernel(TArgs<T> A, T dg, T s, T rowsca
 cpm_status cpm_build_transpose(cpm_ctx *c) {
   cudaStream_t st = c->stream;
   cudaFree(c->d_T_ptr); cudaFree(c->d_T_row); cudaFree(c->d_T_kind); cudaFree(c->d_T_val); cudaFree(c->d_T_val32);
-  cudaFree(c->d_cellid);
+  cudaFree(c->d_cellid); cudaFree(c->d_w1d64); cudaFree(c->d_w1d32);
+  c->d_w1d64 = nullptr; c->d_w1d32 = nullptr;
   c->d_T_ptr = nullptr; c->d_T_row = nullptr; c->d_T_kind = nullptr; c->d_T_val = nullptr; c->d_T_val32 = nullptr;
   c->d_cellid = nullptr;
   c->transpose_ready = false;
@@ -216,6 +223,9 @@ cpm_status cpm_build_transpose(cpm_ctx *c) {
   } while (0)
   TRY(cudaMalloc(&c->d_cellid, sizeof(int32_t) * std::max<int64_t>(nkeys, 1)));
   TRY(cudaMemsetAsync(c->d_cellid, 0xFF, sizeof(int32_t) * std::max<int64_t>(nkeys, 1), st));
+  TRY(cudaMalloc(&c->d_w1d64, sizeof(double) * 12 * std::max<int64_t>(c->NS, 1)));
+  TRY(cudaMalloc(&c->d_w1d32, sizeof(float) * 12 * std::max<int64_t>(c->NS, 1)));
+  w1d_kernel<<<cpm_grid(c->NS, 256), 256, 0, st>>>(c->NS, c->dim, c->d_t64, c->d_w1d64, c->d_w1d32);
   if (c->ncells > 0)
     cellid_kernel<<<cpm_grid(c->ncells, 256), 256, 0, st>>>(c->d_cell_key, c->ncells, c->d_cellid);
   TRY(cudaMalloc(&count, sizeof(int32_t) * (N + 1)));
@@ -264,10 +274,10 @@ cpm_status cpm_apply_transpose_scaled_T(cpm_ctx *c, double m, double n, double r
   A.T_src = c->d_T_row;
   A.T_kind = c->d_T_kind;
   if constexpr (sizeof(T) == 8) {
-    A.t = reinterpret_cast<const T *>(c->d_t64);
+    A.w1d = reinterpret_cast<const T *>(c->d_w1d64);
     A.T_val = reinterpret_cast<const T *>(c->d_T_val);
   } else {
-    A.t = reinterpret_cast<const T *>(c->d_t32);
+    A.w1d = reinterpret_cast<const T *>(c->d_w1d32);
     A.T_val = reinterpret_cast<const T *>(c->d_T_val32);
   }
   T *bv = reinterpret_cast<T *>(c->b_scratch.p);
