@@ -210,6 +210,21 @@ cpm_status cpm_apply_transpose(cpm_ctx *ctx, double m, double n, int prec, const
  * surface values at cp_S(x_i).  FP64, a_dev [N_S] (or [N_S][ld]).  Asynchronous. */
 cpm_status cpm_extend(cpm_ctx *ctx, const double *u_dev, double *a_dev, int nrhs, int64_t ld, void *stream);
 
+/* Surface gradient of a field for the heat method's step 2 (Sec. 7.2): at each
+ * PDE row, central differences (a(x + h e_d) - a(x - h e_d)) / 2h over the FD
+ * neighbours the Laplacian rows use (flipped across curves as in Eq. 11), with
+ * a = E u on PDE DOFs and u on BC DOFs; a missing neighbour takes the row's own
+ * value.  normalize != 0 returns X = -g / |g| (0 where g = 0).  A BC DOF takes
+ * its twin node's value.  u_dev [N], X_dev [N][3] (z = 0 in 2D), FP64.
+ * Allocates its scratch inside the context on first use.  Asynchronous. */
+cpm_status cpm_surface_gradient(cpm_ctx *ctx, const double *u_dev, double *X_dev, int normalize, void *stream);
+
+/* Surface divergence for the heat method's step 3 right-hand side (Sec. 7.2):
+ * b_i = sum_d (X~_d(x_i + h e_d) - X~_d(x_i - h e_d)) / 2h at the PDE rows, with
+ * X~ = E X on PDE DOFs and X on BC DOFs, over the same neighbours as above.
+ * X_dev [N][3], b_dev [N_S], FP64.  Asynchronous. */
+cpm_status cpm_surface_divergence(cpm_ctx *ctx, const double *X_dev, double *b_dev, void *stream);
+
 /* Solves A x = f with diagonal-preconditioned BiCGSTAB (Sec. 5.4), preconditioner
  * diag(m I + n diag L) on PDE rows and 1 on BC rows.  x_dev holds the initial
  * guess on entry.  FP64 mode iterates in FP64.  FP32_IR is mixed-precision

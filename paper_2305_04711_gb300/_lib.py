@@ -23,7 +23,7 @@ NORM_SCALED, NORM_PLAIN = 0, 1
 EXPORTS = ["cpm_band_build", "cpm_band_info", "cpm_export_band", "cpm_set_boundary", "cpm_export_boundary",
            "cpm_rhs", "cpm_apply", "cpm_apply_transpose", "cpm_extend", "cpm_solve", "cpm_solve_adjoint",
            "cpm_boundary_grad", "cpm_destroy", "cpm_status_str", "cpm_diagnostics", "cpm_profile",
-           "cpm_apply_noalloc", "cpm_apply_noalloc_max_bytes"]
+           "cpm_apply_noalloc", "cpm_apply_noalloc_max_bytes", "cpm_surface_gradient", "cpm_surface_divergence"]
 
 
 class ShapeDesc(ctypes.Structure):
@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.cpm_apply_noalloc_max_bytes.argtypes = []
     L.cpm_apply_noalloc_max_bytes.restype = ctypes.c_size_t
     L.cpm_extend.argtypes = [P, P, P, i, i64, P]
+    L.cpm_surface_gradient.argtypes = [P, P, P, i, P]
+    L.cpm_surface_divergence.argtypes = [P, P, P, P]
     L.cpm_solve.argtypes = [P, d, d, P, P, i, i64, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), P]
     L.cpm_solve_adjoint.argtypes = [P, d, d, P, P, i, i64, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), P]
     L.cpm_boundary_grad.argtypes = [P, P, P, i, i64, P]

@@ -199,6 +199,23 @@ class Band:
         L.check(self._lib.cpm_extend(self._h, _ptr(u), _ptr(a), nrhs, ld, _stream()), "cpm_extend")
         return a
 
+    def surface_gradient(self, u: torch.Tensor, normalize: bool = False) -> torch.Tensor:
+        """cpm_surface_gradient: [N, 3] central-difference gradient of the CP
+        extension of u ([N]); normalize gives X = -g / |g|."""
+        _layout(u, self.N)
+        X = torch.empty((self.N, 3), dtype=torch.float64, device="cuda")
+        L.check(self._lib.cpm_surface_gradient(self._h, _ptr(u), _ptr(X), 1 if normalize else 0, _stream()),
+                "cpm_surface_gradient")
+        return X
+
+    def surface_divergence(self, X: torch.Tensor) -> torch.Tensor:
+        """cpm_surface_divergence: [N_S] divergence of the CP extension of X ([N, 3])."""
+        if tuple(X.shape) != (self.N, 3):
+            raise ValueError(f"expected [{self.N}, 3]")
+        b = torch.empty(self.NS, dtype=torch.float64, device="cuda")
+        L.check(self._lib.cpm_surface_divergence(self._h, _ptr(X), _ptr(b), _stream()), "cpm_surface_divergence")
+        return b
+
     def solve(self, m: float, n: float, f: torch.Tensor, x0: Optional[torch.Tensor] = None, tol: float = 1e-10,
               maxit: int = 20000, mode: str = "fp64", inner_tol: float = 0.0, max_refine: int = 0,
               check_every: int = 16, adjoint: bool = False, raise_on_error: bool = True, norm: str = "scaled",

@@ -39,6 +39,7 @@ void cpm_destroy(cpm_ctx *c) {
   cudaFree(c->d_shape_c);
   cudaFree(c->a_scratch.p);
   cudaFree(c->b_scratch.p);
+  cudaFree(c->heat_scratch.p);
   cudaFree(c->d_err);
   cudaFree(c->d_counter);
   for (auto e : c->prof.ev) cudaEventDestroy(e);
@@ -172,6 +173,18 @@ cpm_status cpm_apply_transpose(cpm_ctx *c, double m, double n, int prec, const v
   if (prec == CPM_PREC_FP32)
     return cpm_apply_transpose_T<float>(c, m, n, (const float *)u, (float *)v, nrhs, ld, as_stream(stream));
   return CPM_ERR_ARG;
+}
+
+cpm_status cpm_surface_gradient(cpm_ctx *c, const double *u, double *X, int normalize, void *stream) {
+  if (!c || !u || !X) return CPM_ERR_ARG;
+  if (!c->boundary_set) return CPM_ERR_STATE;
+  return cpm_internal_surface_gradient(c, u, X, normalize, as_stream(stream));
+}
+
+cpm_status cpm_surface_divergence(cpm_ctx *c, const double *X, double *b, void *stream) {
+  if (!c || !X || !b) return CPM_ERR_ARG;
+  if (!c->boundary_set) return CPM_ERR_STATE;
+  return cpm_internal_surface_divergence(c, X, b, as_stream(stream));
 }
 
 cpm_status cpm_extend(cpm_ctx *c, const double *u, double *a, int nrhs, int64_t ld, void *stream) {

@@ -52,6 +52,8 @@ template <typename T>
 int cpm_launch_gather_cells(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld,
                             cudaStream_t st, bool diff, int rpl);
 
+cpm_status cpm_internal_surface_gradient(cpm_ctx *c, const double *u, double *X, int normalize, cudaStream_t st);
+cpm_status cpm_internal_surface_divergence(cpm_ctx *c, const double *X, double *b, cudaStream_t st);
 cpm_status cpm_internal_extend(cpm_ctx *c, const double *u, double *a, int nrhs, int64_t ld, cudaStream_t st);
 cpm_status cpm_internal_rhs(cpm_ctx *c, const double *s, const double *g, const double *samples, double *f, int nrhs,
                             int64_t ld, cudaStream_t st);

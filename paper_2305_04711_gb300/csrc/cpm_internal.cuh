@@ -160,6 +160,7 @@ struct cpm_ctx {
   // scratch
   WorkBuf a_scratch;                // E u intermediate
   WorkBuf b_scratch;                // transposed FD intermediate
+  WorkBuf heat_scratch;             // extended fields of the gradient / divergence
   unsigned *d_err = nullptr;        // device error flags
   unsigned long long *d_counter = nullptr;  // diagnostics counters [4]
   int64_t noflip_twin = 0;
