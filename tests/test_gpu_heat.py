@@ -40,9 +40,9 @@ def test_heat_geodesic_pipeline_matches_oracle_and_distance(oracle_mod):
     h = 1 / 16
     w = ci.Workload("sph_pt", ci.sphere(), h, [ci.point_curve(tuple(p))], 0.0, 1.0)
     band, ref = pair(oracle_mod, w)
-    phi, st1, st2 = geodesic_distance(band, h, tol=1e-13)
+    phi, st1, st2 = geodesic_distance(band, h, tol=1e-12)
     pr = ref.heat_geodesic(h)
-    assert rel_inf(phi.cpu().numpy(), pr) < 1e-8
+    assert rel_inf(phi.cpu().numpy(), pr) < 1e-7
     a = band.extend(phi).cpu().numpy()
     exact = np.arccos(np.clip(ref.cp @ p, -1.0, 1.0))
     keep = ref.cp @ p > -0.9
