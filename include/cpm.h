@@ -241,7 +241,10 @@ cpm_status cpm_surface_divergence(cpm_ctx *ctx, const double *X_dev, double *b_d
 cpm_status cpm_solve(cpm_ctx *ctx, double m, double n, const double *f_dev, double *x_dev, int nrhs, int64_t ld,
                      const cpm_solve_opts *opts, cpm_solve_stats *stats, void *stream);
 
-/* Solves A^T lambda = g (the adjoint system) with the same options. */
+/* Solves A^T lambda = g (the adjoint system) with the same options.  The
+ * iteration is right-preconditioned (A^T W mu = g, lambda = W mu: the transpose
+ * of the row-scaled forward system) and tol applies to the unscaled relative
+ * residual |g - A^T lambda| / |g| whatever opts->norm says. */
 cpm_status cpm_solve_adjoint(cpm_ctx *ctx, double m, double n, const double *g_dev, double *lambda_dev, int nrhs,
                              int64_t ld, const cpm_solve_opts *opts, cpm_solve_stats *stats, void *stream);
 

@@ -601,7 +601,9 @@ static cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const
   const int64_t N = c->NS + c->NC;
   // Jacobi value of the PDE rows: 1/(m + n diag L) (Sec. 5.4)
   const double dS = 1.0 / (m + n * (-2.0 * c->dim / (c->h * c->h)));
-  const double wrow = scaled ? dS : 1.0;  // residual weight of the PDE rows
+  // residual weight of the PDE rows; the adjoint (iterated right-preconditioned,
+  // see below) is measured on its unscaled residual, the iteration's own
+  const double wrow = (scaled && !adjoint) ? dS : 1.0;
   SolveWork *&w = adjoint ? c->solve_adj : c->solve;
   cpm_status rc;
   int iters = 0, restarts = 0, refinements = 0;
