@@ -435,7 +435,10 @@ cpm_status cpm_apply_scaled_T(cpm_ctx *c, double m, double n, double rowscale, c
     launched = launch_batched<T, 2>(c, A, (T)m, (T)n, (T)rowscale, u, a, v, nrhs, ld, st, diff);
   else if (nrhs >= 16 && nrhs <= 32)
     launched = launch_batched<T, 1>(c, A, (T)m, (T)n, (T)rowscale, u, a, v, nrhs, ld, st, diff);
-  else {
+  else if (nrhs == 1 && c->ncells > 0) {
+    launched = 1 + cpm_launch_gather1<T>(c, A, u, a, st, diff);
+    cpm_launch_combine<T>(A, (T)m, (T)n, (T)rowscale, u, a, v, nrhs, ld, st, diff);
+  } else {
     cpm_launch_gather<T>(A, u, a, nrhs, ld, st, diff);
     cpm_launch_combine<T>(A, (T)m, (T)n, (T)rowscale, u, a, v, nrhs, ld, st, diff);
   }

@@ -54,6 +54,11 @@ int cpm_launch_gather_cells(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u,
 
 cpm_status cpm_internal_surface_gradient(cpm_ctx *c, const double *u, double *X, int normalize, cudaStream_t st);
 cpm_status cpm_internal_surface_divergence(cpm_ctx *c, const double *X, double *b, cudaStream_t st);
+// single right-hand side: E u for all PDE rows in cell order plus the
+// flipped-entry correction; returns the number of kernels launched
+template <typename T>
+int cpm_launch_gather1(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u, T *a, cudaStream_t st, bool diff);
+
 cpm_status cpm_internal_extend(cpm_ctx *c, const double *u, double *a, int nrhs, int64_t ld, cudaStream_t st);
 cpm_status cpm_internal_rhs(cpm_ctx *c, const double *s, const double *g, const double *samples, double *f, int nrhs,
                             int64_t ld, cudaStream_t st);

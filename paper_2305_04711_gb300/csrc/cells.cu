@@ -331,12 +331,85 @@ __global__ void __launch_bounds__(256) correct_kernel(const int32_t *__restrict_
   }
 }
 
+// per cell the start of each of its 16 (2D: 4) stencil lines along x: s0 the
+// DOF of the line's first node; s1 the DOF of its first node past the brick's
+// x face where the line crosses it (-1 otherwise)
+__global__ void cell_lines_kernel(BandView v, const uint32_t *cell_key, int64_t ncells, int2 *lines) {
+  const int nl = (v.dim == 3) ? 16 : 4;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncells * 16;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cid = t >> 4;
+    const int ln = (int)(t & 15);
+    int2 out = make_int2(-1, -1);
+    if (ln < nl) {
+      const uint32_t key = cell_key[cid];
+      const int32_t b = (int32_t)(key >> 9);
+      const int l = (int)(key & 511u);
+      const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+      const int cy = ln & 3, cz = ln >> 2;
+      out.x = cpm_node_index(v, b, lx, ly + cy, lz + cz);
+      if (lx + 3 >= 8) out.y = cpm_node_index(v, b, 8, ly + cy, lz + cz);
+    }
+    lines[t] = out;
+  }
+}
+
+__global__ void row_cell_kernel(const int32_t *cell_start, int64_t ncells, int32_t *row_cell) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x)
+    for (int32_t q = cell_start[c]; q < cell_start[c + 1]; ++q) row_cell[q] = (int32_t)c;
+}
+
+// single right-hand side: one thread per PDE row, rows taken in cell order so
+// that the rows of a cell (same 64 nodes) run in neighbouring threads and share
+// the cell's line table and node values in cache
+template <typename T, bool DIFF, int DIM>
+__global__ void __launch_bounds__(256) gather1_kernel(ApplyArgs<T> A, const int32_t *__restrict__ crows,
+                                                      const int32_t *__restrict__ row_cell,
+                                                      const uint32_t *__restrict__ ckey,
+                                                      const int2 *__restrict__ lines, int64_t NS,
+                                                      const T *__restrict__ u, T *__restrict__ a) {
+  constexpr int NZ = (DIM == 3) ? 4 : 1;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < NS; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = __ldg(crows + q);
+    const int32_t cid = __ldg(row_cell + q);
+    const int lx = (int)(__ldg(ckey + cid) & 7u);
+    const int split = (lx + 3 < 8) ? 4 : 8 - lx;
+    const int2 *ln = lines + (int64_t)cid * 16;
+    T wx[4], wy[4], wz[4];
+    cpm_lagrange4<T>(__ldg(A.t + 3 * row), wx);
+    cpm_lagrange4<T>(__ldg(A.t + 3 * row + 1), wy);
+    if (DIM == 3) cpm_lagrange4<T>(__ldg(A.t + 3 * row + 2), wz);
+    else { wz[0] = T(1); wz[1] = wz[2] = wz[3] = T(0); }
+    const T uc = DIFF ? __ldg(u + __ldg(&ln[0].x)) : T(0);
+    T acc = T(0);
+#pragma unroll
+    for (int cz = 0; cz < NZ; ++cz) {
+      T pz = T(0);
+#pragma unroll
+      for (int cy = 0; cy < 4; ++cy) {
+        const int2 se = __ldg(ln + cz * 4 + cy);
+        T line = T(0);
+#pragma unroll
+        for (int cx = 0; cx < 4; ++cx) {
+          const int32_t idx = (cx < split) ? (se.x + cx) : (se.y + (cx - split));
+          line += wx[cx] * (__ldg(u + idx) - uc);
+        }
+        pz += wy[cy] * line;
+      }
+      acc += wz[cz] * pz;
+    }
+    if (DIFF) acc += uc - __ldg(u + row);
+    a[row] = acc;
+  }
+}
+
 }  // namespace
 
 void cpm_free_cells(cpm_ctx *c) {
   cudaFree(c->d_cell_start); cudaFree(c->d_cell_rows); cudaFree(c->d_cell_key); cudaFree(c->d_nbr8);
   cudaFree(c->d_corr_row); cudaFree(c->d_corr_start); cudaFree(c->d_corr_node); cudaFree(c->d_corr_col);
-  cudaFree(c->d_corr_w64); cudaFree(c->d_corr_w32);
+  cudaFree(c->d_corr_w64); cudaFree(c->d_corr_w32); cudaFree(c->d_cell_lines); cudaFree(c->d_row_cell);
+  c->d_cell_lines = nullptr; c->d_row_cell = nullptr;
   c->d_cell_start = nullptr; c->d_cell_rows = nullptr; c->d_cell_key = nullptr; c->d_nbr8 = nullptr;
   c->d_corr_row = nullptr; c->d_corr_start = nullptr; c->d_corr_node = nullptr; c->d_corr_col = nullptr;
   c->d_corr_w64 = nullptr; c->d_corr_w32 = nullptr;
@@ -381,6 +454,13 @@ cpm_status cpm_build_cells(cpm_ctx *c) {
   cell_finish_kernel<<<cpm_grid(nkeys, 256), 256, 0, st>>>(count, offs, cellpos, nkeys, c->d_cell_rows,
                                                            c->d_cell_start, c->d_cell_key);
   set_i32_kernel<<<1, 1, 0, st>>>(c->d_cell_start + c->ncells, h_tot);
+  TRY(cudaMalloc(&c->d_cell_lines, sizeof(int2) * 16 * std::max<int64_t>(c->ncells, 1)));
+  TRY(cudaMalloc(&c->d_row_cell, sizeof(int32_t) * std::max<int64_t>(c->NS, 1)));
+  if (c->ncells > 0) {
+    cell_lines_kernel<<<cpm_grid(c->ncells * 16, 256), 256, 0, st>>>(c->view(), c->d_cell_key, c->ncells,
+                                                                    reinterpret_cast<int2 *>(c->d_cell_lines));
+    row_cell_kernel<<<cpm_grid(c->ncells, 256), 256, 0, st>>>(c->d_cell_start, c->ncells, c->d_row_cell);
+  }
   TRY(cudaMalloc(&c->d_nbr8, sizeof(int32_t) * 8 * std::max<int64_t>(c->NS, 1)));
   nbr8_kernel<<<cpm_grid(c->NS, 256), 256, 0, st>>>(c->view(), c->d_rself, c->d_rbase, c->d_spec_of, c->d_spec_fcol,
                                                     c->d_nbr8);
@@ -467,3 +547,31 @@ template int cpm_launch_gather_cells<float>(const cpm_ctx *, const ApplyArgs<flo
                                             int64_t, cudaStream_t, bool, int);
 template int cpm_launch_gather_cells<double>(const cpm_ctx *, const ApplyArgs<double> &, const double *, double *,
                                              int, int64_t, cudaStream_t, bool, int);
+
+template <typename T>
+int cpm_launch_gather1(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u, T *a, cudaStream_t st, bool diff) {
+  if (c->ncells == 0) return 0;
+  const unsigned g = cpm_grid(c->NS, 256);
+  const int2 *lines = reinterpret_cast<const int2 *>(c->d_cell_lines);
+  if (c->dim == 3) {
+    if (diff) gather1_kernel<T, true, 3><<<g, 256, 0, st>>>(A, c->d_cell_rows, c->d_row_cell, c->d_cell_key, lines, c->NS, u, a);
+    else gather1_kernel<T, false, 3><<<g, 256, 0, st>>>(A, c->d_cell_rows, c->d_row_cell, c->d_cell_key, lines, c->NS, u, a);
+  } else {
+    if (diff) gather1_kernel<T, true, 2><<<g, 256, 0, st>>>(A, c->d_cell_rows, c->d_row_cell, c->d_cell_key, lines, c->NS, u, a);
+    else gather1_kernel<T, false, 2><<<g, 256, 0, st>>>(A, c->d_cell_rows, c->d_row_cell, c->d_cell_key, lines, c->NS, u, a);
+  }
+  if (c->ncorr > 0) {
+    const T *cw;
+    if constexpr (sizeof(T) == 8) cw = reinterpret_cast<const T *>(c->d_corr_w64);
+    else cw = reinterpret_cast<const T *>(c->d_corr_w32);
+    unsigned gc = (unsigned)std::min<int64_t>((c->ncorr + 7) / 8, 152 * 16);
+    correct_kernel<T, 1><<<gc, 256, 0, st>>>(c->d_corr_row, c->d_corr_start, c->d_corr_node, c->d_corr_col, cw,
+                                             c->ncorr, u, a, 1, 1);
+    return 2;
+  }
+  return 1;
+}
+template int cpm_launch_gather1<float>(const cpm_ctx *, const ApplyArgs<float> &, const float *, float *, cudaStream_t,
+                                       bool);
+template int cpm_launch_gather1<double>(const cpm_ctx *, const ApplyArgs<double> &, const double *, double *,
+                                        cudaStream_t, bool);

@@ -137,6 +137,8 @@ struct cpm_ctx {
   int32_t *d_cell_rows = nullptr;   // [nbulk] (nbulk = NS)
   uint32_t *d_cell_key = nullptr;   // [ncells] packed base location (brick << 9 | local)
   int32_t *d_nbr8 = nullptr;        // [NS][8] FD neighbour columns (6 used; flipped near curves)
+  int32_t *d_cell_lines = nullptr;  // [ncells][16] int2 line starts of each cell's stencil
+  int32_t *d_row_cell = nullptr;    // [NS] cell of each position of cell_rows
   // flipped interpolation entries of the special rows: row i's E entry at node
   // corr_node holds column corr_col instead (a BC DOF), weight corr_w
   int64_t ncorr = 0, ncorr_ent = 0;
