@@ -104,7 +104,25 @@ __global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, 
       const T ui = __ldg(u + i * ld + r);
       T s = T(0);
       int present = 0;
-      if (rb & CPM_SPECIAL_BIT) {
+      if (A.nbr8) {
+        // the precomputed neighbour table (flipped columns included)
+        const int4 n0 = __ldg(reinterpret_cast<const int4 *>(A.nbr8 + i * 8));
+        const int2 n1 = __ldg(reinterpret_cast<const int2 *>(A.nbr8 + i * 8 + 4));
+        const int32_t nb[6] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const int32_t c = nb[k];
+          if (c < 0) continue;
+          ++present;
+          if (c < NS) {
+            const T ac = __ldg(a + (int64_t)c * ld + r);
+            s += DIFF ? ac + (__ldg(u + (int64_t)c * ld + r) - ui) : ac;
+          } else {
+            const T uc = __ldg(u + (int64_t)c * ld + r);
+            s += DIFF ? (uc - ui) : uc;
+          }
+        }
+      } else if (rb & CPM_SPECIAL_BIT) {
         int64_t sp = __ldg(A.spec_of + i);
         for (int k = 0; k < 6; ++k) {
           int32_t c = __ldg(A.fcol + sp * 6 + k);

@@ -403,6 +403,22 @@ __global__ void __launch_bounds__(256) gather1_kernel(ApplyArgs<T> A, const int3
   }
 }
 
+// single right-hand side correction: one thread per row with flipped entries
+template <typename T>
+__global__ void __launch_bounds__(256) correct1_kernel(const int32_t *__restrict__ crow,
+                                                       const int32_t *__restrict__ cstart,
+                                                       const int32_t *__restrict__ cnode,
+                                                       const int32_t *__restrict__ ccol, const T *__restrict__ cw,
+                                                       int64_t ncorr, const T *__restrict__ u, T *__restrict__ a) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < ncorr; q += (int64_t)gridDim.x * blockDim.x) {
+    T acc = T(0);
+    const int32_t e1 = __ldg(cstart + q + 1);
+    for (int32_t e = __ldg(cstart + q); e < e1; ++e)
+      acc += __ldg(cw + e) * (__ldg(u + __ldg(ccol + e)) - __ldg(u + __ldg(cnode + e)));
+    a[__ldg(crow + q)] += acc;
+  }
+}
+
 }  // namespace
 
 void cpm_free_cells(cpm_ctx *c) {
@@ -564,9 +580,8 @@ int cpm_launch_gather1(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u, T *a
     const T *cw;
     if constexpr (sizeof(T) == 8) cw = reinterpret_cast<const T *>(c->d_corr_w64);
     else cw = reinterpret_cast<const T *>(c->d_corr_w32);
-    unsigned gc = (unsigned)std::min<int64_t>((c->ncorr + 7) / 8, 152 * 16);
-    correct_kernel<T, 1><<<gc, 256, 0, st>>>(c->d_corr_row, c->d_corr_start, c->d_corr_node, c->d_corr_col, cw,
-                                             c->ncorr, u, a, 1, 1);
+    correct1_kernel<T><<<cpm_grid(c->ncorr, 256), 256, 0, st>>>(c->d_corr_row, c->d_corr_start, c->d_corr_node,
+                                                                c->d_corr_col, cw, c->ncorr, u, a);
     return 2;
   }
   return 1;
