@@ -349,8 +349,8 @@ def run_ours(args):
             "config": wl.describe(band.N), "clocks": clocks, "e2e": e2e, "gpu_launches": int(prof["launches"])}
     if rank == 0:
         last = stats[-1]
-        line["solve"] = {"iterations": last.iterations, "refinements": last.refinements, "relres_max": last.relres,
-                         "status": last.status}
+        line["solve"] = {"iterations": last.iterations, "fp64_iterations": last.fp64_iterations,
+                         "refinements": last.refinements, "relres_max": last.relres, "status": last.status}
         # roofline of the dominant kernel (the batched FP32 product), timed live
         per_launch_ms = prof["apply_ms"] / max(prof["applies"], 1)
         rows_per_launch = prof["row_rhs"] / max(prof["applies"], 1)

@@ -122,6 +122,7 @@ typedef struct {
   double relres;     /* final FP64 relative residual |W (f - A x)| / |W f| in the chosen norm (max over
                         right-hand sides) */
   int status;        /* cpm_status of this solve */
+  int fp64_iterations; /* iterations run in FP64 (all of them in FP64 mode; the FP64 finish in FP32_IR) */
 } cpm_solve_stats;
 
 typedef struct cpm_ctx cpm_ctx;

@@ -47,7 +47,7 @@ class SolveOpts(ctypes.Structure):
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int), ("restarts", ctypes.c_int),
-                ("relres", ctypes.c_double), ("status", ctypes.c_int)]
+                ("relres", ctypes.c_double), ("status", ctypes.c_int), ("fp64_iterations", ctypes.c_int)]
 
 
 _lib = None

@@ -50,6 +50,7 @@ class SolveStats:
     restarts: int
     relres: float
     status: str
+    fp64_iterations: int = 0
 
 
 def shape_desc(shape) -> tuple:
@@ -228,7 +229,8 @@ class Band:
         fn = self._lib.cpm_solve_adjoint if adjoint else self._lib.cpm_solve
         rc = fn(self._h, float(m), float(n), _ptr(f), _ptr(x), nrhs, ld, ctypes.byref(o), ctypes.byref(st),
                 _stream())
-        stats = SolveStats(st.iterations, st.refinements, st.restarts, st.relres, L.STATUS.get(rc, str(rc)))
+        stats = SolveStats(st.iterations, st.refinements, st.restarts, st.relres, L.STATUS.get(rc, str(rc)),
+                           st.fp64_iterations)
         if raise_on_error:
             L.check(rc, "cpm_solve_adjoint" if adjoint else "cpm_solve")
         return x, stats

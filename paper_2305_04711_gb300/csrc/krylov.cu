@@ -606,7 +606,7 @@ static cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const
   const double wrow = (scaled && !adjoint) ? dS : 1.0;
   SolveWork *&w = adjoint ? c->solve_adj : c->solve;
   cpm_status rc;
-  int iters = 0, restarts = 0, refinements = 0;
+  int iters = 0, restarts = 0, refinements = 0, iters64 = 0;
   bool broke = false;
   std::vector<double> rn2, fn2;
   ApplyFn<double> ap64 = adjoint ? cpm_apply_transpose_scaled_T<double> : cpm_apply_scaled_T<double>;
@@ -635,6 +635,7 @@ static cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const
                             &broke, st);
       if (rc) return rc;
       iters += it;
+      iters64 += it;
       restarts += rs;
       rc = residual64(c, ap64, m, n, f, x, w, wrow, rn2, fn2, st);
       if (rc) return rc;
@@ -674,6 +675,7 @@ static cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const
                             &rs, &broke, st);
       if (rc) return rc;
       iters += it;
+      iters64 += it;
       restarts += rs;
       rc = residual64(c, ap64, m, n, f, x, w64, wrow, rn2, fn2, st);
       if (rc) return rc;
@@ -690,6 +692,7 @@ static cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const
     stats->restarts = restarts;
     stats->relres = relres;
     stats->status = out;
+    stats->fp64_iterations = iters64;
   }
   return out;
 }
