@@ -50,6 +50,25 @@ FLOPS_ROW_RHS_FP32 = 246.0
 SMS, FP32_LANES = 152, 128
 
 
+def max_over_ranks(ms: float) -> float:
+    """The slowest rank's time (all ranks get it); the value itself without a
+    process group.  Replicas share nothing else: no collective on the data path."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(ms)
+    dev = "cuda" if tdist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def seconds_per_rhs(ms: float, steps: int, nrhs: int, world: int) -> float:
+    """Whole-job metric: wall time of the timed steps over every right-hand side
+    that all ranks solved in them (weak scaling: each rank solves its own batch)."""
+    return (ms / 1000.0) / (steps * nrhs * world)
+
+
 def profiled_traffic():
     """DRAM bytes per batched product from the committed ncu summary (None if absent)."""
     import re
@@ -324,14 +343,10 @@ def run_ours(args):
         ev1.record()
         barrier()
     prof = band.profile(False)
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
     log(f"timed: {ms / args.steps:.1f} ms/step {stats[-1]}")
     ms_per_step = ms / args.steps
-    value = (ms / 1000.0) / (args.steps * NRHS * world)
+    value = seconds_per_rhs(ms, args.steps, NRHS, world)
     clocks = clk.summary()
     hbm, sm_max, peak_src = peaks()
 
