@@ -203,7 +203,14 @@ cpm_status cpm_apply_noalloc(cpm_ctx *ctx, double m, double n, int prec, const v
 /* Size in bytes of cpm_apply_noalloc's fixed intermediate array. */
 size_t cpm_apply_noalloc_max_bytes(void);
 
-/* v = A^T u (the transposed product, by a cell-bucketed gather: no atomics). */
+/* v = A^T u, the transpose of cpm_apply's operator (the adjoint of Sec. 5.4's
+ * product, needed for gradients of losses of the solution).  Same arguments,
+ * precisions and layouts as cpm_apply.  Computed as gathers, without atomics:
+ * b = (n/h^2) F_S^T u over the unflipped FD entries, then per node E^T b from the
+ * rows of the stencil cells that hold it, plus per-column lists of the flipped FD
+ * and E entries and of the BC-row entries built in cpm_set_boundary.  Its
+ * intermediate b lives in the context's scratch (grown on first use).
+ * Asynchronous.  Errors: ARG, STATE (no boundary set), OOM, CUDA. */
 cpm_status cpm_apply_transpose(cpm_ctx *ctx, double m, double n, int prec, const void *u_dev, void *v_dev, int nrhs,
                                int64_t ld, void *stream);
 
