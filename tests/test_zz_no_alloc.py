@@ -1,6 +1,14 @@
-"""cpm_apply_noalloc (the product with the library's fixed intermediate array)
-against cpm_apply.  This file is collected last so that it also runs after
-every other test has used the library on the same device."""
+"""cpm_apply_noalloc against cpm_apply.
+
+cpm_apply_noalloc is the operator product for callers that cannot allocate
+device memory while they call it -- a host framework that has already handed
+the whole device to its own memory pool (a cudaMalloc would fail), or a
+latency-bound caller that cannot afford the device synchronisation that
+cudaMalloc/cudaFree imply.  It keeps its intermediate in one fixed array inside
+the library.  These tests check its result against cpm_apply on two calls in a
+row (the array keeps the previous call's contents) and that an oversized call is
+refused.  The file is collected last so that it also runs after every other test
+has used the library on the same device."""
 import numpy as np
 import pytest
 
