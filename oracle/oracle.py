@@ -355,6 +355,19 @@ class Oracle:
             b += self._central(at, a, nb, d)
         return b
 
+    def heat_cn(self, u0: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
+        """Crank-Nicolson steps of u_t = Delta_S u (the time stepping of the
+        convergence studies, Sec. 6.2): (I - dt/2 M) u^{k+1} = (I + dt/2 M) u^k,
+        with the BC rows of both sides as assembled (Dirichlet data held fixed)."""
+        lu = spla.splu(self.A(1.0, -0.5 * dt).tocsc())
+        Ap = self.A(1.0, 0.5 * dt)
+        u = np.asarray(u0, dtype=np.float64).copy()
+        for _ in range(nsteps):
+            rhs = Ap @ u
+            rhs[self.NS:] = u[self.NS:]
+            u = lu.solve(rhs)
+        return u
+
     def heat_geodesic(self, dt: float, extra: int = 0) -> np.ndarray:
         """The heat method of Sec. 7.2 with the curves as the distance source:
         (1) one implicit Euler step (I - dt M) v = 0 off C, v = 1 on C;
