@@ -21,7 +21,7 @@ import numpy as np
 
 SH_CIRCLE, SH_SPHERE, SH_TORUS, SH_BUMPY = 1, 2, 3, 4
 CV_POINT, CV_CIRCLE = 1, 2
-BC_DIR1, BC_DIR2 = 1, 2
+BC_DIR1, BC_DIR2, BC_NEU1, BC_NEU2 = 1, 2, 3, 4
 
 
 @dataclasses.dataclass
@@ -54,6 +54,7 @@ class Curve:
     rad: float = 0.0
     ref: Sequence[float] = (1.0, 0.0, 0.0)
     two_sided: bool = False
+    bc_minus: int = 0        # BC type on the minus side (0: the same as bc, the plus side's)
 
 
 @dataclasses.dataclass

@@ -13,7 +13,9 @@
  *   - tube radius, Eq. (3) "bandwidth"; band Omega(S) and BFS, Alg. 1, Sec. 5.1
  *   - barycentric Lagrange interpolation (E), Eq. (1); FD Laplacian (L), Eq. (2)
  *   - BC DOFs Omega(C), Sec. 4.1; crossing test Eqs. (8)-(9), Sec. 4.2
- *   - stencil modification Eqs. (10)-(11), Sec. 4.3; Dirichlet IBC rows, Sec. 4.3
+ *   - stencil modification Eqs. (10)-(11), Sec. 4.3; Dirichlet and zero-Neumann
+ *     IBC rows of first and second order, with a BC type per side, Sec. 4.3
+ *   - interpolation degree p = 3 (cubic) or p = 2 (quadratic, Sec. 7), Eq. (3)
  *   - localisation 2 r_Omega, Sec. 4.6
  *   - M = diag(L) + (L - diag L) E, Sec. 5.3; A = mI + nM and the four-step
  *     partially matrix-free product, Sec. 5.4; diagonal-preconditioned BiCGSTAB
@@ -45,7 +47,7 @@
 
 enum { SH_CIRCLE = 1, SH_SPHERE = 2, SH_TORUS = 3, SH_BUMPY = 4 };
 enum { CV_POINT = 1, CV_CIRCLE = 2 };
-enum { BC_DIR1 = 1, BC_DIR2 = 2 };
+enum { BC_DIR1 = 1, BC_DIR2 = 2, BC_NEU1 = 3, BC_NEU2 = 4 };
 
 typedef struct {
   int kind;      /* SH_* */
@@ -69,6 +71,7 @@ typedef struct {
   double rad;        /* circle radius */
   double ref[3];     /* circle: unit reference direction in its plane (angle 0) */
   int two_sided;     /* 0: one value set for both sides; 1: separate sets per side */
+  int bc_minus;      /* BC type on the minus side (0: the same as bc, which is the plus side's) */
 } orc_curve;
 
 /* ------------------------------------------------------------------ */
@@ -306,6 +309,7 @@ typedef struct orc_ctx {
   orc_shape sh;
   double *sh_a, *sh_c;
   int dim;
+  int p;         /* interpolation degree (3 or 2); p + 1 stencil nodes per axis */
   double h, rband;
   int64_t NS, NC;
   int32_t *ijk;  /* [NS*3] */
@@ -320,6 +324,7 @@ typedef struct orc_ctx {
   int32_t *bc_curve;  /* [NC] */
   double *cpc;        /* [NC*3]: cp_C(x_alpha) */
   int32_t *bc_side;   /* [NC]: +1/-1/0: side of S_perp holding cp_S(x_alpha) */
+  int32_t *bc_type;   /* [NC]: BC type of the row: that of the side opposite cp_S(x_alpha) */
   int64_t n_noflip_twin; /* diagnostics: flip requested but no twin existed */
   /* operator */
   csr E;      /* N_S rows (PDE DOFs) x N columns: interpolation with flips */
@@ -352,14 +357,14 @@ void orc_destroy(orc_ctx *c) {
   if (!c) return;
   free(c->sh_a); free(c->sh_c); free(c->ijk); free(c->cp); hm_free(&c->index);
   free(c->curves); free(c->bc_of); free(c->near_c); free(c->twin); free(c->bc_curve);
-  free(c->cpc); free(c->bc_side);
+  free(c->cpc); free(c->bc_side); free(c->bc_type);
   csr_free(&c->E); csr_free(&c->Loff); csr_free(&c->B);
   free(c);
 }
 
-/* Eq. (3): r = dx sqrt((d-1)((p+1)/2)^2 + (q+(p+1)/2)^2), p = 3, q = 1 */
-double orc_tube_radius(int dim, double h) {
-  double half = (3.0 + 1.0) / 2.0;
+/* Eq. (3): r = dx sqrt((d-1)((p+1)/2)^2 + (q+(p+1)/2)^2) with q = 1 */
+double orc_tube_radius(int dim, int p, double h) {
+  double half = ((double)p + 1.0) / 2.0;
   return h * sqrt((double)(dim - 1) * (half * half) + (1.0 + half) * (1.0 + half));
 }
 
@@ -386,8 +391,8 @@ static int cmp_canon(const void *a, const void *b) {
 
 /* Alg. 1: BFS from a node near S over the 2d axis neighbours, keeping nodes
  * with |x - cp_S(x)| <= r; then sort into the canonical order. */
-int orc_build(const orc_shape *sh, double h, double rband, orc_ctx **out) {
-  if (!sh || !out || h <= 0) return ORC_ERR_ARG;
+int orc_build(const orc_shape *sh, double h, int p, double rband, orc_ctx **out) {
+  if (!sh || !out || h <= 0 || (p != 2 && p != 3)) return ORC_ERR_ARG;
   orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
   if (!c) return ORC_ERR_OOM;
   c->sh = *sh;
@@ -398,8 +403,8 @@ int orc_build(const orc_shape *sh, double h, double rband, orc_ctx **out) {
     memcpy(c->sh_c, sh->c, sizeof(double) * 3 * sh->K);
     c->sh.a = c->sh_a; c->sh.c = c->sh_c;
   }
-  c->dim = sh->dim; c->h = h;
-  c->rband = rband > 0 ? rband : orc_tube_radius(sh->dim, h);
+  c->dim = sh->dim; c->h = h; c->p = p;
+  c->rband = rband > 0 ? rband : orc_tube_radius(sh->dim, p, h);
   int seed[3] = {(int)lround(sh->seed[0] / h), (int)lround(sh->seed[1] / h), sh->dim == 3 ? (int)lround(sh->seed[2] / h) : 0};
   hmap visited;
   if (hm_init(&visited, 1 << 16)) { orc_destroy(c); return ORC_ERR_OOM; }
@@ -462,10 +467,10 @@ done:
 }
 
 /* brute-force band over a box of integer indices (a pin for Alg. 1) */
-int64_t orc_band_bruteforce(const orc_shape *sh, double h, double rband, const int *lo, const int *hi, int32_t *out, int64_t cap) {
+int64_t orc_band_bruteforce(const orc_shape *sh, double h, int p, double rband, const int *lo, const int *hi, int32_t *out, int64_t cap) {
   orc_ctx c;
   memset(&c, 0, sizeof(c));
-  c.sh = *sh; c.dim = sh->dim; c.h = h; c.rband = rband > 0 ? rband : orc_tube_radius(sh->dim, h);
+  c.sh = *sh; c.dim = sh->dim; c.h = h; c.p = p; c.rband = rband > 0 ? rband : orc_tube_radius(sh->dim, p, h);
   int64_t n = 0;
   int klo = sh->dim == 3 ? lo[2] : 0, khi = sh->dim == 3 ? hi[2] : 0;
   for (int k = klo; k <= khi; ++k)
@@ -499,27 +504,33 @@ void orc_cpc(const orc_curve *cv, const double *x, double *out) { cp_C(cv, x, ou
 
 /* ------------------------------------------------------------------ */
 /* Interpolation weights: barycentric Lagrange form (Sec. 3.2, Berrut & Trefethen)
- * on the equispaced nodes 0,1,2,3 in units of dx; weights lambda_j proportional
- * to (-1)^j C(3,j).  Exact hit on a node gives the Kronecker delta.          */
-void orc_bary_weights(double t, double w[4]) {
-  static const double lam[4] = {1.0, -3.0, 3.0, -1.0};
-  for (int j = 0; j < 4; ++j)
+ * of degree p on the equispaced nodes 0..p in units of dx; weights lambda_j
+ * proportional to (-1)^j C(p,j).  Exact hit on a node gives the Kronecker delta. */
+void orc_bary_weights(int p, double t, double *w) {
+  static const double lam3[4] = {1.0, -3.0, 3.0, -1.0};
+  static const double lam2[3] = {1.0, -2.0, 1.0};
+  const double *lam = (p == 2) ? lam2 : lam3;
+  const int n = p + 1;
+  for (int j = 0; j < n; ++j)
     if (t == (double)j) {
-      for (int k = 0; k < 4; ++k) w[k] = (k == j) ? 1.0 : 0.0;
+      for (int k = 0; k < n; ++k) w[k] = (k == j) ? 1.0 : 0.0;
       return;
     }
   double q[4], s = 0.0;
-  for (int j = 0; j < 4; ++j) { q[j] = lam[j] / (t - (double)j); s += q[j]; }
-  for (int j = 0; j < 4; ++j) w[j] = q[j] / s;
+  for (int j = 0; j < n; ++j) { q[j] = lam[j] / (t - (double)j); s += q[j]; }
+  for (int j = 0; j < n; ++j) w[j] = q[j] / s;
 }
 
-/* stencil of a query point y: base node floor(y/dx) - 1 per axis (so that the
- * point lies between stencil nodes 1 and 2) and t = y/dx - base */
+/* stencil of a query point y: the p + 1 nodes per axis nearest to y.  Cubic:
+ * base floor(y/dx) - 1, so that y lies between stencil nodes 1 and 2.
+ * Quadratic: base floor(y/dx + 1/2) - 1, so that node 1 is the nearest node
+ * and every stencil node lies within 1.5 dx of y, the half-width (p+1)/2 that
+ * Eq. (3) assumes.  t = y/dx - base. */
 static void stencil_of(const orc_ctx *c, const double *y, int base[3], double t[3]) {
   for (int a = 0; a < 3; ++a) {
     if (a >= c->dim) { base[a] = 0; t[a] = 0.0; continue; }
     double s = y[a] / c->h;
-    base[a] = (int)floor(s) - 1;
+    base[a] = (c->p == 2) ? (int)floor(s + 0.5) - 1 : (int)floor(s) - 1;
     t[a] = s - (double)base[a];
   }
 }
@@ -548,10 +559,11 @@ static void cpdiff(const orc_ctx *c, const orc_curve *cv, int64_t node, double z
   int base[3];
   double t[3];
   stencil_of(c, c->cp + 3 * node, base, t);
-  int nz = (c->dim == 3) ? 4 : 1;
+  const int np1 = c->p + 1;
+  int nz = (c->dim == 3) ? np1 : 1;
   for (int cz = 0; cz < nz; ++cz)
-    for (int cy = 0; cy < 4; ++cy)
-      for (int cx = 0; cx < 4; ++cx) {
+    for (int cy = 0; cy < np1; ++cy)
+      for (int cx = 0; cx < np1; ++cx) {
         int64_t j = hm_get(&c->index, node_key(base[0] + cx, base[1] + cy, c->dim == 3 ? base[2] + cz : 0));
         if (j < 0) continue;
         double w[3];
@@ -584,6 +596,8 @@ static int cmp_i64pair(const void *a, const void *b) {
 int orc_set_curves(orc_ctx *c, const orc_curve *curves, int ncurves) {
   if (!c || ncurves < 0) return ORC_ERR_ARG;
   free(c->curves); free(c->bc_of); free(c->near_c); free(c->twin); free(c->bc_curve); free(c->cpc); free(c->bc_side);
+  free(c->bc_type);
+  c->bc_type = NULL;
   c->assembled = 0;
   c->ncurves = ncurves;
   c->curves = (orc_curve *)malloc(sizeof(orc_curve) * (ncurves > 0 ? ncurves : 1));
@@ -615,6 +629,7 @@ int orc_set_curves(orc_ctx *c, const orc_curve *curves, int ncurves) {
   c->bc_curve = (int32_t *)malloc(sizeof(int32_t) * (nc ? nc : 1));
   c->cpc = (double *)malloc(sizeof(double) * 3 * (nc ? nc : 1));
   c->bc_side = (int32_t *)malloc(sizeof(int32_t) * (nc ? nc : 1));
+  c->bc_type = (int32_t *)malloc(sizeof(int32_t) * (nc ? nc : 1));
   for (int64_t a = 0; a < nc; ++a) {
     int k = (int)list[2 * a];
     int64_t j = list[2 * a + 1];
@@ -627,16 +642,22 @@ int orc_set_curves(orc_ctx *c, const orc_curve *curves, int ncurves) {
     cpdiff(c, &c->curves[k], j, z);
     double s = dot3(z, c->curves[k].nu);
     c->bc_side[a] = (c->curves[k].kind == CV_POINT && c->dim == 3) ? 0 : (s > 0) - (s < 0);
+    /* a BC DOF stands in for its node as seen from the other side of C, so its
+     * equation is the BC of the side opposite cp_S(x_alpha) (Sec. 4.2: mixed
+     * types, one per side) */
+    int bminus = c->curves[k].bc_minus ? c->curves[k].bc_minus : c->curves[k].bc;
+    c->bc_type[a] = (c->bc_side[a] > 0) ? bminus : c->curves[k].bc;
   }
   free(list);
   return 0;
 }
 
-void orc_export_bc(const orc_ctx *c, int64_t *twin, int32_t *curve, double *cpc, int32_t *side) {
+void orc_export_bc(const orc_ctx *c, int64_t *twin, int32_t *curve, double *cpc, int32_t *side, int32_t *type) {
   if (twin) memcpy(twin, c->twin, sizeof(int64_t) * c->NC);
   if (curve) memcpy(curve, c->bc_curve, sizeof(int32_t) * c->NC);
   if (cpc) memcpy(cpc, c->cpc, sizeof(double) * 3 * c->NC);
   if (side) memcpy(side, c->bc_side, sizeof(int32_t) * c->NC);
+  if (type) memcpy(type, c->bc_type, sizeof(int32_t) * c->NC);
 }
 void orc_export_near(const orc_ctx *c, int32_t *near_c, int64_t *bc_of) {
   if (near_c) memcpy(near_c, c->near_c, sizeof(int32_t) * c->NS);
@@ -671,19 +692,25 @@ static int64_t bc_col(orc_ctx *c, int k, const double *dstar, int64_t j) {
 }
 
 /* Assemble E (Eq. 1 with Eq. 10 flips), the off-diagonal part of L (Eq. 2 with
- * the same flips) and the BC rows (Sec. 4.3; reading: Dirichlet BC rows are the
- * BC equations themselves, u_alpha = g (1st order) or
- * u_alpha + sum wbar u = 2 g (2nd order, stencil at cpbar_C = cp_S(2 cp_C - x))).
- * A missing FD neighbour (band edge) contributes nothing. */
+ * the same flips) and the BC rows (Sec. 4.3).  Reading: BC rows are the BC
+ * equations themselves, with the type of the side the BC DOF stands in for:
+ *   first-order Dirichlet   u_alpha                    = g
+ *   second-order Dirichlet  u_alpha + sum wbar u       = 2 g   (stencil at cpbar_C)
+ *   first-order Neumann     u_alpha - sum w u          = 0     (stencil at cp_C)
+ *   second-order Neumann    u_alpha - sum wbar u       = 0     (stencil at cpbar_C)
+ * with the mirror point cpbar_C = cp_S(2 cp_C - x) of Sec. 4.3.  A missing FD
+ * neighbour (band edge) contributes nothing. */
 int orc_assemble(orc_ctx *c) {
   if (!c) return ORC_ERR_ARG;
   int64_t NS = c->NS, NC = c->NC;
   int d = c->dim;
-  int npts = (d == 3) ? 64 : 16;
+  const int np1 = c->p + 1;
+  int npts = (d == 3) ? np1 * np1 * np1 : np1 * np1;
   c->n_noflip_twin = 0;
   if (csr_begin(&c->E, NS, NS * npts) || csr_begin(&c->Loff, NS, NS * 2 * d) || csr_begin(&c->B, NC, NC * (npts + 1)))
     return ORC_ERR_OOM;
   double inv_h2 = 1.0 / (c->h * c->h);
+  int nz = (d == 3) ? np1 : 1;
   for (int64_t i = 0; i < NS; ++i) {
     int k = c->near_c[i];
     double dstar[3] = {0, 0, 0};
@@ -691,11 +718,10 @@ int orc_assemble(orc_ctx *c) {
     int base[3];
     double t[3], w[3][4] = {{0}};
     stencil_of(c, c->cp + 3 * i, base, t);
-    for (int a = 0; a < d; ++a) orc_bary_weights(t[a], w[a]);
-    int nz = (d == 3) ? 4 : 1;
+    for (int a = 0; a < d; ++a) orc_bary_weights(c->p, t[a], w[a]);
     for (int cz = 0; cz < nz; ++cz)
-      for (int cy = 0; cy < 4; ++cy)
-        for (int cx = 0; cx < 4; ++cx) {
+      for (int cy = 0; cy < np1; ++cy)
+        for (int cx = 0; cx < np1; ++cx) {
           int64_t j = hm_get(&c->index, node_key(base[0] + cx, base[1] + cy, d == 3 ? base[2] + cz : 0));
           if (j < 0) return ORC_ERR_STATE; /* an interpolation node outside the band */
           double wt = w[0][cx] * w[1][cy];
@@ -717,28 +743,36 @@ int orc_assemble(orc_ctx *c) {
   for (int64_t a = 0; a < NC; ++a) {
     int k = c->bc_curve[a];
     int64_t j = c->twin[a];
+    int type = c->bc_type[a];
     if (csr_push(&c->B, NS + a, 1.0)) return ORC_ERR_OOM;
-    if (c->curves[k].bc == BC_DIR2) {
-      double dstar[3], x[3], y[3], cpb[3];
+    if (type != BC_DIR1) {
+      double dstar[3], x[3], q[3];
       cpdiff(c, &c->curves[k], j, dstar);
-      node_x(c, c->ijk + 3 * j, x);
       const double *cc = c->cpc + 3 * a;
-      for (int e = 0; e < 3; ++e) y[e] = 2.0 * cc[e] - x[e];
-      int err = cp_S(&c->sh, y, cpb);
-      if (err) return err;
+      if (type == BC_NEU1) {
+        /* first-order Neumann: the query point is cp_C(x_alpha) itself */
+        q[0] = cc[0]; q[1] = cc[1]; q[2] = cc[2];
+      } else {
+        /* second order: the mirror point cpbar_C = cp_S(2 cp_C - x) (Sec. 4.3) */
+        double y[3];
+        node_x(c, c->ijk + 3 * j, x);
+        for (int e = 0; e < 3; ++e) y[e] = 2.0 * cc[e] - x[e];
+        int err = cp_S(&c->sh, y, q);
+        if (err) return err;
+      }
+      const double sgn = (type == BC_DIR2) ? 1.0 : -1.0;
       int base[3];
       double t[3], w[3][4] = {{0}};
-      stencil_of(c, cpb, base, t);
-      for (int e = 0; e < d; ++e) orc_bary_weights(t[e], w[e]);
-      int nz = (d == 3) ? 4 : 1;
+      stencil_of(c, q, base, t);
+      for (int e = 0; e < d; ++e) orc_bary_weights(c->p, t[e], w[e]);
       for (int cz = 0; cz < nz; ++cz)
-        for (int cy = 0; cy < 4; ++cy)
-          for (int cx = 0; cx < 4; ++cx) {
-            int64_t q = hm_get(&c->index, node_key(base[0] + cx, base[1] + cy, d == 3 ? base[2] + cz : 0));
-            if (q < 0) return ORC_ERR_STATE;
+        for (int cy = 0; cy < np1; ++cy)
+          for (int cx = 0; cx < np1; ++cx) {
+            int64_t qn = hm_get(&c->index, node_key(base[0] + cx, base[1] + cy, d == 3 ? base[2] + cz : 0));
+            if (qn < 0) return ORC_ERR_STATE;
             double wt = w[0][cx] * w[1][cy];
             if (d == 3) wt = wt * w[2][cz];
-            if (csr_push(&c->B, bc_col(c, k, dstar, q), wt)) return ORC_ERR_OOM;
+            if (csr_push(&c->B, bc_col(c, k, dstar, qn), sgn * wt)) return ORC_ERR_OOM;
           }
     }
     c->B.ptr[a + 1] = c->B.nnz;

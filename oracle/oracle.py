@@ -9,7 +9,8 @@ uses scipy for the sparse algebra a reader can check by eye:
   * direct solves with scipy's SuperLU    (the paper uses Eigen's SparseLU, Sec. 6.1)
   * the adjoint through A^T               (a CSR transpose)
   * Dirichlet data: f_alpha = c_alpha g(cp_C(x_alpha)) with c = 1 (1st order)
-    or 2 (2nd order), g taken from the side opposite cp_S(x_alpha) (Sec. 4.3)
+    or 2 (2nd order), g taken from the side opposite cp_S(x_alpha) (Sec. 4.3);
+    zero-Neumann rows carry no data (c = 0)
 
 It shares no code with the CUDA library and never imports it.
 """
@@ -54,7 +55,7 @@ class _Shape(ctypes.Structure):
 class _Curve(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("bc", ctypes.c_int), ("p", ctypes.c_double * 3),
                 ("nu", ctypes.c_double * 3), ("rad", ctypes.c_double), ("ref", ctypes.c_double * 3),
-                ("two_sided", ctypes.c_int)]
+                ("two_sided", ctypes.c_int), ("bc_minus", ctypes.c_int)]
 
 
 _lib = None
@@ -66,16 +67,16 @@ def lib():
         L = ctypes.CDLL(build())
         P = ctypes.c_void_p
         d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int
-        L.orc_build.argtypes = [ctypes.POINTER(_Shape), d, d, ctypes.POINTER(P)]
+        L.orc_build.argtypes = [ctypes.POINTER(_Shape), d, i32, d, ctypes.POINTER(P)]
         L.orc_destroy.argtypes = [P]
         L.orc_ns.argtypes = [P]; L.orc_ns.restype = i64
         L.orc_nc.argtypes = [P]; L.orc_nc.restype = i64
         L.orc_rband.argtypes = [P]; L.orc_rband.restype = d
-        L.orc_tube_radius.argtypes = [i32, d]; L.orc_tube_radius.restype = d
+        L.orc_tube_radius.argtypes = [i32, i32, d]; L.orc_tube_radius.restype = d
         L.orc_export_band.argtypes = [P, P, P]
         L.orc_lookup.argtypes = [P, i32, i32, i32]; L.orc_lookup.restype = i64
         L.orc_set_curves.argtypes = [P, ctypes.POINTER(_Curve), i32]
-        L.orc_export_bc.argtypes = [P, P, P, P, P]
+        L.orc_export_bc.argtypes = [P, P, P, P, P, P]
         L.orc_export_near.argtypes = [P, P, P]
         L.orc_assemble.argtypes = [P]
         L.orc_noflip_twin.argtypes = [P]; L.orc_noflip_twin.restype = i64
@@ -84,12 +85,12 @@ def lib():
         L.orc_apply.argtypes = [P, d, d, P, P, P]
         L.orc_extend.argtypes = [P, P, P]
         L.orc_bicgstab.argtypes = [P, d, d, P, P, d, i32, ctypes.POINTER(i32), ctypes.POINTER(d)]
-        L.orc_band_bruteforce.argtypes = [ctypes.POINTER(_Shape), d, d, P, P, P, i64]
+        L.orc_band_bruteforce.argtypes = [ctypes.POINTER(_Shape), d, i32, d, P, P, P, i64]
         L.orc_band_bruteforce.restype = i64
         L.orc_cp.argtypes = [ctypes.POINTER(_Shape), P, P]
         L.orc_bumpy_phi.argtypes = [ctypes.POINTER(_Shape), P, P, P, P]
         L.orc_cpc.argtypes = [ctypes.POINTER(_Curve), P, P]
-        L.orc_bary_weights.argtypes = [d, P]
+        L.orc_bary_weights.argtypes = [i32, d, P]
         L.orc_num_threads.restype = i32
         _lib = L
     return _lib
@@ -125,17 +126,18 @@ def make_curves(curves: Sequence[ci.Curve]):
             c.p[k] = float(cv.p[k]); c.nu[k] = float(cv.nu[k]); c.ref[k] = float(cv.ref[k])
         c.rad = cv.rad
         c.two_sided = int(cv.two_sided)
+        c.bc_minus = int(getattr(cv, "bc_minus", 0) or 0)
     return arr
 
 
-def tube_radius(dim: int, h: float) -> float:
-    return lib().orc_tube_radius(dim, h)
+def tube_radius(dim: int, h: float, p: int = 3) -> float:
+    return lib().orc_tube_radius(dim, p, h)
 
 
-def bary_weights(t: float) -> np.ndarray:
+def bary_weights(t: float, p: int = 3) -> np.ndarray:
     w = np.zeros(4)
-    lib().orc_bary_weights(t, _ptr(w))
-    return w
+    lib().orc_bary_weights(p, t, _ptr(w))
+    return w[:p + 1]
 
 
 def closest_point(sh: ci.Shape, x) -> np.ndarray:
@@ -163,13 +165,13 @@ def curve_cp(cv: ci.Curve, x) -> np.ndarray:
     return out
 
 
-def band_bruteforce(sh: ci.Shape, h: float, lo, hi, rband: float = -1.0) -> np.ndarray:
+def band_bruteforce(sh: ci.Shape, h: float, lo, hi, rband: float = -1.0, p: int = 3) -> np.ndarray:
     s, keep = make_shape(sh)
     lo = np.array(list(lo) + [0] * (3 - len(lo)), dtype=np.int32)
     hi = np.array(list(hi) + [0] * (3 - len(hi)), dtype=np.int32)
-    n = lib().orc_band_bruteforce(ctypes.byref(s), h, rband, _ptr(lo), _ptr(hi), None, 0)
+    n = lib().orc_band_bruteforce(ctypes.byref(s), h, p, rband, _ptr(lo), _ptr(hi), None, 0)
     out = np.zeros((max(n, 1), 3), dtype=np.int32)
-    lib().orc_band_bruteforce(ctypes.byref(s), h, rband, _ptr(lo), _ptr(hi), _ptr(out), n)
+    lib().orc_band_bruteforce(ctypes.byref(s), h, p, rband, _ptr(lo), _ptr(hi), _ptr(out), n)
     return out[:n]
 
 
@@ -188,12 +190,12 @@ def _check(rc):
 class Oracle:
     """The discrete CPM of the paper on one band; FP64 throughout."""
 
-    def __init__(self, shape: ci.Shape, h: float, rband: float = -1.0):
-        self.shape, self.h = shape, h
+    def __init__(self, shape: ci.Shape, h: float, rband: float = -1.0, p: int = 3):
+        self.shape, self.h, self.p = shape, h, p
         self.dim = shape.dim
         s, self._keep = make_shape(shape)
         self._h = ctypes.c_void_p()
-        _check(lib().orc_build(ctypes.byref(s), h, rband, ctypes.byref(self._h)))
+        _check(lib().orc_build(ctypes.byref(s), h, p, rband, ctypes.byref(self._h)))
         self.NS = lib().orc_ns(self._h)
         self.NC = 0
         self.rband = lib().orc_rband(self._h)
@@ -230,9 +232,12 @@ class Oracle:
         self.bc_curve = np.zeros(nc, dtype=np.int32)
         self.cpc = np.zeros((nc, 3), dtype=np.float64)
         self.bc_side = np.zeros(nc, dtype=np.int32)
-        lib().orc_export_bc(self._h, _ptr(self.twin), _ptr(self.bc_curve), _ptr(self.cpc), _ptr(self.bc_side))
+        self.bc_type = np.zeros(nc, dtype=np.int32)
+        lib().orc_export_bc(self._h, _ptr(self.twin), _ptr(self.bc_curve), _ptr(self.cpc), _ptr(self.bc_side),
+                            _ptr(self.bc_type))
         self.twin, self.bc_curve = self.twin[:self.NC], self.bc_curve[:self.NC]
         self.cpc, self.bc_side = self.cpc[:self.NC], self.bc_side[:self.NC]
+        self.bc_type = self.bc_type[:self.NC]
         self.near_c = np.zeros(self.NS, dtype=np.int32)
         self.bc_of = np.zeros(self.NS, dtype=np.int64)
         lib().orc_export_near(self._h, _ptr(self.near_c), _ptr(self.bc_of))
@@ -355,16 +360,25 @@ class Oracle:
             b += self._central(at, a, nb, d)
         return b
 
-    def heat_cn(self, u0: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
+    def heat_cn(self, u0: np.ndarray, dt: float, nsteps: int, g_bc=None) -> np.ndarray:
         """Crank-Nicolson steps of u_t = Delta_S u (the time stepping of the
-        convergence studies, Sec. 6.2): (I - dt/2 M) u^{k+1} = (I + dt/2 M) u^k,
-        with the BC rows of both sides as assembled (Dirichlet data held fixed)."""
+        convergence studies, Sec. 6.2): (I - dt/2 M) u^{k+1} = (I + dt/2 M) u^k on
+        the PDE rows, while the BC rows of step k+1 are the BC equations with the
+        data of time t_{k+1}: right-hand side c_alpha g_alpha(t_{k+1}) (c = 1, 2
+        for first- and second-order Dirichlet rows, 0 for zero-Neumann rows).
+        g_bc: per BC DOF values, an array held fixed in time or a function of t;
+        None means zero data."""
         lu = spla.splu(self.A(1.0, -0.5 * dt).tocsc())
         Ap = self.A(1.0, 0.5 * dt)
+        cb = self.bc_scale() if self.NC else np.zeros(0)
         u = np.asarray(u0, dtype=np.float64).copy()
-        for _ in range(nsteps):
+        for k in range(nsteps):
             rhs = Ap @ u
-            rhs[self.NS:] = u[self.NS:]
+            if callable(g_bc):
+                g = np.asarray(g_bc((k + 1) * dt), dtype=np.float64)
+            else:
+                g = np.zeros(self.NC) if g_bc is None else np.asarray(g_bc, dtype=np.float64)
+            rhs[self.NS:] = cb * g
             u = lu.solve(rhs)
         return u
 
@@ -420,8 +434,9 @@ class Oracle:
         return out
 
     def bc_scale(self) -> np.ndarray:
-        """c_alpha: 1 for first-order and 2 for second-order Dirichlet rows."""
-        return np.array([2.0 if self.curves[k].bc == ci.BC_DIR2 else 1.0 for k in self.bc_curve])
+        """c_alpha: 1 for first-order and 2 for second-order Dirichlet rows, 0 for
+        zero-Neumann rows (per BC DOF: the type of the side it stands in for)."""
+        return np.array([{ci.BC_DIR1: 1.0, ci.BC_DIR2: 2.0}.get(int(t), 0.0) for t in self.bc_type])
 
     def sample_matrix(self, nsamples: Sequence[int]) -> sp.csr_matrix:
         """B: per-curve periodic linear interpolation of samples (taken at angles
