@@ -1,21 +1,26 @@
 #!/usr/bin/env python
-"""Benchmark of the CPM hot path on GB300: batched FP32 + FP64-refinement solves
-against plain FP64 solves.
+"""Benchmark of the CPM hot path on GB300: the batched FP32 + FP64-refinement
+solve of a diffusion-curve batch, against plain FP64 solves.
 
-Default workload (one step), the unit-sphere configuration at h = 1/128
-(about 1.76M DOFs): the Dirichlet latitude circles theta = pi/4 and 3 pi/4
-with a batch of 64 Poisson problems -Delta_S u = l(l+1) Y_l^m, the circles
-carrying Y_l^m, for the first 64 real spherical harmonics with 1 <= l <= 8
-(the exact solution of column k is Y_l^m itself).  One step solves the 64
-together by mixed-precision iterative refinement (FP32 BiCGSTAB inner solves, FP64
-residuals and solution) to a Jacobi-scaled
-relative residual of 1e-10.  The metric is seconds per right-hand side.
-Alongside: the plain FP64 solve of one right-hand side of the same workload,
-the single-RHS operator product's algorithmic bandwidth against the measured
-HBM peak, the dominant kernel's roofline (timed live during the timed region by
-the library's event pairs), an end-to-end number through host buffers, and the
-CPU oracle as baseline.  --workload torus runs the torus batch instead
-(R = 1, r = 0.4, h = 1/256, 8 meridians, 64 right-hand sides U[0,1]).
+Default workload (one step): the torus R = 1, r = 0.4 at h = 1/256 (about
+8.8M DOFs) with 8 Dirichlet meridians at seeded toroidal angles carrying 64
+right-hand sides with values U[0,1] (the per-channel diffusion-curve solves of
+Sec. 7.1).  One step solves the 64 together by mixed-precision iterative
+refinement (FP32 BiCGSTAB with FP64 residual replacement) to the paper's
+stopping test |f - A x|_2 <= 1e-10 |f|_2 per right-hand side (Sec. 5.4).  The
+metric is seconds per right-hand side.  Alongside:
+  * the plain FP64 solve of one right-hand side (and, with --fp64-batch, of the
+    64 as one FP64 batch), and both results' distance to each other and to the
+    closed form (piecewise linear in the toroidal angle between meridians);
+  * the dominant kernel's roofline: the batched FP32 operator product, timed by
+    the library's event pairs right after the timed region, against the FP32
+    FMA peak of this device's SM count and clock;
+  * cpm_apply bandwidth for one right-hand side (FP32 and FP64) on the bumpy
+    sphere band at h = 1/640 (about 42M DOFs), against the measured HBM peak;
+  * an end-to-end number through host buffers, and the CPU oracle timed on the
+    same band and right-hand side.
+--workload sphere runs the unit sphere at h = 1/128 with a batch of 64
+spherical-harmonic Poisson problems instead.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -44,10 +49,17 @@ TOL = 1e-10
 #        FP64 u, v (8 + 8) + FP64 t (24) + base (4)
 BYTES_ROW_FP32 = 24.0
 BYTES_ROW_FP64 = 44.0
-# flops per row and right-hand side of the FP32 product: 84 FMA of the separable
-# 4x4x4 gather (168), 64 difference subtractions, 14 for the 7-point combine
-FLOPS_ROW_RHS_FP32 = 246.0
-SMS, FP32_LANES = 152, 128
+# flops per row of one product: separable 4x4x4 gather 84 FMA (168), Lagrange
+# weights ~36, 7-point combine with m, n ~12; batched, per row and right-hand
+# side: 168 + 12 plus the weights shared by the batch
+FLOPS_ROW_FP64 = 215.0
+
+
+def flops_row_rhs_batched(nrhs: int) -> float:
+    return 168.0 + 12.0 + 36.0 / nrhs
+
+
+GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_torus256_iterations.json")
 
 
 def max_over_ranks(ms: float) -> float:
@@ -69,17 +81,6 @@ def seconds_per_rhs(ms: float, steps: int, nrhs: int, world: int) -> float:
     return (ms / 1000.0) / (steps * nrhs * world)
 
 
-def profiled_traffic():
-    """DRAM bytes per batched product from the committed ncu summary (None if absent)."""
-    import re
-    p = os.path.join(ROOT, "profiles", "batched_product_sphere128_64rhs.md")
-    try:
-        m = re.search(r"traffic_bytes_per_product:\s*(\d+)", open(p).read())
-        return int(m.group(1)) if m else None
-    except OSError:
-        return None
-
-
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -89,17 +90,34 @@ def peaks():
     return 6800.0, 2070.0, "fallback"
 
 
-def parse():
+def profiled_traffic(name: str):
+    """DRAM bytes per launch from a committed ncu summary (None if absent)."""
+    import re
+    p = os.path.join(ROOT, "profiles", name)
+    try:
+        m = re.search(r"traffic_bytes_per_product:\s*(\d+)", open(p).read())
+        return int(m.group(1)) if m else None
+    except OSError:
+        return None
+
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "torus"])
+    ap.add_argument("--workload", default="torus", choices=["torus", "sphere"])
     ap.add_argument("--h", type=float, default=0.0, help="grid spacing (0: the workload's own)")
-    ap.add_argument("--maxit", type=int, default=20000)
+    ap.add_argument("--maxit", type=int, default=40000)
+    ap.add_argument("--warmup-maxit", type=int, default=64,
+                    help="iteration cap of each (untimed) warm-up solve; 0 = full solves")
+    ap.add_argument("--apply-h", type=float, default=1.0 / 640,
+                    help="grid spacing of the bumpy-sphere band for the apply bandwidth (0: skip)")
+    ap.add_argument("--fp64-batch", action="store_true", help="also time the 64 right-hand sides as an FP64 batch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--cpu-iters", type=int, default=0, help="oracle iterations timed per sample (0: auto)")
+    return ap.parse_args(argv)
 
 
 def ylm_pairs(n):
@@ -112,7 +130,7 @@ def ylm_pairs(n):
 
 class Workload:
     """The benchmark problem: geometry, boundary, and a batch of right-hand
-    sides built through the library (cpm_rhs) from per-BC-DOF values."""
+    sides built through the library (cpm_rhs) from the curve data."""
 
     def __init__(self, kind, h):
         import cpm_inputs as ci
@@ -121,6 +139,7 @@ class Workload:
             self.h = h or 1.0 / 128
             self.w = ci.config2(self.h, ci.BC_DIR1)
             self.n_samples = None
+            self.ang = self.g = None
         else:
             self.h = h or 1.0 / 256
             self.w, self.ang, self.g = ci.config3(h=self.h, ncurves=8, nrhs=NRHS, seed=0, min_gap=0.2)
@@ -130,42 +149,49 @@ class Workload:
         if self.kind == "sphere":
             wl = (f"unit sphere, h=1/{round(1 / self.h)}, Dirichlet circles theta=pi/4, 3pi/4; {NRHS} Poisson "
                   f"problems -Delta u = l(l+1) Y_l^m with the circles carrying Y_l^m (first {NRHS} real harmonics, "
-                  f"1<=l<=8); batched mixed-precision refinement (FP32 BiCGSTAB inner solves, FP64 residuals) to a Jacobi-scaled relative residual "
-                  f"of {TOL:g}")
+                  f"1<=l<=8)")
         else:
             wl = (f"torus R=1 r=0.4, h=1/{round(1 / self.h)}, 8 Dirichlet meridians (seeded angles, min gap 0.2 "
-                  f"rad), {NRHS} right-hand sides U[0,1]; batched mixed-precision refinement (FP32 BiCGSTAB inner solves) to a "
-                  f"Jacobi-scaled relative residual of {TOL:g}")
-        d = {"workload": wl, "nrhs": NRHS, "tol": TOL, "norm": "Jacobi-scaled residual",
-             "l2": "inputs larger than L2 (each [N][64] Krylov vector is several hundred MB vs 129 MB L2)"}
+                  f"rad), {NRHS} right-hand sides with U[0,1] meridian values (diffusion-curve channels)")
+        wl += (f"; one batched FP32+FP64-refinement solve (FP32 BiCGSTAB, FP64 residual replacement) per step to "
+               f"|f - A x|_2 <= {TOL:g} |f|_2")
+        d = {"workload": wl, "nrhs": NRHS, "tol": TOL, "norm": "|f - A x|_2 / |f|_2 per right-hand side (Sec. 5.4)",
+             "l2": "inputs larger than L2 (each [N][64] Krylov vector is hundreds of MB vs 129 MB L2)"}
         if N is not None:
             d["N"] = int(N)
         return d
 
-    def host_inputs(self, band):
-        """(s [NS][64] or None, g [NC][64]) as host arrays; for the sphere from
-        the exported closest points (input data only)."""
+    def host_inputs(self, NS, NC, cp, cpc):
+        """Host input array of one batch: the torus meridian values [8][64], or
+        for the sphere [s; g] at the exported closest points."""
         import numpy as np
-        import torch
         import cpm_inputs as ci
         if self.kind == "torus":
-            return None, None
-        _, cp = band.export_band()
-        cpc = band.export_boundary()["cpc"].cpu().numpy()
-        cp = cp.cpu().numpy()
-        s = np.zeros((band.NS, NRHS))
-        g = np.zeros((band.NC, NRHS))
+            return np.ascontiguousarray(self.g)
+        s = np.zeros((NS, NRHS))
+        g = np.zeros((NC, NRHS))
         for k, (l, m) in enumerate(ylm_pairs(NRHS)):
-            # M u = -f with f = l(l+1) Y: source of the row equations (m=0, n=1)
             s[:, k] = -l * (l + 1) * ci.real_ylm(l, m, cp)
             g[:, k] = ci.real_ylm(l, m, cpc)
-        return s, g
+        return np.concatenate([s, g], axis=0)
 
-    def exact(self, band, col):
+    def exact(self, cp, col):
+        """Closed form of column col at the closest points: Y_l^m (sphere), or
+        piecewise linear in the toroidal angle between meridians (torus: Delta_S
+        u = u_phiphi / (R + r cos psi)^2 for u = u(phi))."""
+        import numpy as np
         import cpm_inputs as ci
-        _, cp = band.export_band()
-        l, m = ylm_pairs(NRHS)[col]
-        return ci.real_ylm(l, m, cp.cpu().numpy())
+        if self.kind == "sphere":
+            l, m = ylm_pairs(NRHS)[col]
+            return ci.real_ylm(l, m, cp)
+        phi = np.arctan2(cp[:, 1], cp[:, 0]) % (2 * math.pi)
+        a = np.asarray(self.ang) % (2 * math.pi)
+        order = np.argsort(a)
+        a, gv = a[order], self.g[order, col]
+        a_ext = np.concatenate([a, [a[0] + 2 * math.pi]])
+        g_ext = np.concatenate([gv, [gv[0]]])
+        p = np.where(phi < a[0], phi + 2 * math.pi, phi)
+        return np.interp(p, a_ext, g_ext)
 
 
 # --------------------------------------------------------------------------
@@ -224,62 +250,140 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------
-def cpu_baseline_sample(kind):
-    """The oracle as it stands (plain C, OpenMP) on the same workload at a
-    coarser grid sized for tens of seconds of CPU work: band, assembly and one
-    BiCGSTAB solve of one right-hand side to 1e-10.  Returns its time per DOF
-    per iteration, used to project s/RHS to the full workload."""
-    import numpy as np
-    import cpm_inputs as ci
-    from oracle import oracle as O
-    O.build()
-    h = 1.0 / 48 if kind == "sphere" else 1.0 / 64
-    wl = Workload(kind, h)
-    t0 = time.perf_counter()
-    o = O.Oracle(wl.w.shape, h).set_curves(wl.w.curves)
-    t_setup = time.perf_counter() - t0
-    if kind == "sphere":
-        f = o.rhs(-2 * 3 * ci.real_ylm(2, 1, o.cp), ci.real_ylm(2, 1, o.cpc))
-    else:
-        f = o.rhs(np.zeros(o.NS), wl.g[:, 0][o.bc_curve])
-    t0 = time.perf_counter()
-    x, it, rr = o.bicgstab(0.0, 1.0, f, tol=TOL, maxit=20000)
-    t_solve = time.perf_counter() - t0
-    return {"N": o.N, "h": h, "iters": it, "relres": rr, "t_solve": t_solve, "t_setup": t_setup,
-            "s_per_dof_iter": t_solve / (o.N * max(it, 1)), "cores": O.n_threads()}
+class OracleSample:
+    """The CPU oracle as it stands on the benchmark's own band: set up once
+    (untimed), then a bounded number of its BiCGSTAB iterations on right-hand
+    side column 0 are timed per sample."""
+
+    def __init__(self, wl):
+        import numpy as np
+        from oracle import oracle as O
+        O.build()
+        self.O = O
+        t0 = time.perf_counter()
+        self.o = O.Oracle(wl.w.shape, wl.h).set_curves(wl.w.curves)
+        self.t_setup = time.perf_counter() - t0
+        o = self.o
+        if wl.kind == "torus":
+            self.f = o.rhs(np.zeros(o.NS), wl.g[:, 0][o.bc_curve])
+        else:
+            import cpm_inputs as ci
+            l, m = ylm_pairs(NRHS)[0]
+            self.f = o.rhs(-l * (l + 1) * ci.real_ylm(l, m, o.cp), ci.real_ylm(l, m, o.cpc))
+        self.cores = O.n_threads()
+
+    def time_iterations(self, n: int) -> float:
+        """Seconds per BiCGSTAB iteration, from n iterations from x = 0 (the
+        initial product included)."""
+        t0 = time.perf_counter()
+        try:
+            self.o.bicgstab(0.0, 1.0, self.f, tol=1e-300, maxit=n)
+        except self.O.OracleError:
+            pass  # NOT_CONVERGED after n iterations: the expected outcome
+        return (time.perf_counter() - t0) / n
+
+    def full_solve(self):
+        t0 = time.perf_counter()
+        x, it, rr = self.o.bicgstab(0.0, 1.0, self.f, tol=TOL, maxit=40000)
+        return time.perf_counter() - t0, it, rr
+
+
+def golden_iterations(wl):
+    """The oracle's own iteration count on the default torus workload, recorded
+    by oracle/record_iterations.py (None for other workloads or if absent)."""
+    if wl.kind != "torus" or abs(wl.h - 1.0 / 256) > 1e-15:
+        return None
+    try:
+        with open(GOLDEN_ITERS) as fh:
+            return json.load(fh)
+    except OSError:
+        return None
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle, each step a bounded sample of the
-    workload (see cpu_baseline_sample), projected to s/RHS of the full one:
-    the band grows like h^-2 and BiCGSTAB's iteration count like 1/h."""
+    """--impl reference: the CPU oracle on the host cores.  Small bands are
+    solved completely per step; on the default workload each step times a
+    bounded run of oracle BiCGSTAB iterations on the full band and the value is
+    that per-iteration time times the oracle's own iteration count to 1e-10."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     wl = Workload(args.workload, args.h)
-    samples = []
+    ref = OracleSample(wl)
+    N = ref.o.N
+    gold = golden_iterations(wl)
+    full = N <= 400_000
+    times, per_it, its = [], [], None
+    n_it = args.cpu_iters or 8
     for k in range(args.warmup + args.steps):
-        s = cpu_baseline_sample(args.workload)
+        if full:
+            t, it, rr = ref.full_solve()
+            its = it
+            per = t / max(it, 1)
+        else:
+            per = ref.time_iterations(n_it)
+            t = per * n_it
         if k >= args.warmup:
-            samples.append(s)
-    s = samples[-1]
-    n_full = s["N"] * (s["h"] / wl.h) ** 2
-    it_full = s["iters"] * s["h"] / wl.h
-    per = sum(x["s_per_dof_iter"] for x in samples) / len(samples)
-    value = per * n_full * it_full
-    sample = (f"oracle BiCGSTAB solve of 1 RHS on the same geometry at h=1/{round(1 / s['h'])} ({s['N']} DOF, "
-              f"{s['iters']} iterations, {s['t_solve']:.1f} s); time per DOF-iteration scaled to {n_full:.3g} DOF x "
-              f"{it_full:.0f} iterations (band ~ h^-2, iterations ~ 1/h)")
+            times.append(t)
+            per_it.append(per)
+    per = sum(per_it) / len(per_it)
+    if full:
+        value = sum(times) / len(times)
+        sample = f"complete oracle BiCGSTAB solve of 1 RHS ({N} DOF, {its} iterations) per step, measured"
+        iters, src = its, "measured in this run"
+    elif gold is not None:
+        iters, src = gold["iterations"], f"the oracle's own solve ({GOLDEN_ITERS[len(ROOT) + 1:]})"
+        value = per * iters
+        sample = (f"{n_it} oracle BiCGSTAB iterations on the full band ({N} DOF) per step, timed: "
+                  f"{per:.3f} s/iteration x {iters} iterations ({src}); projected")
+    else:
+        print(json.dumps({"impl": "reference", "unavailable": "no oracle iteration count recorded for this "
+                          "workload (run oracle/record_iterations.py)"}), flush=True)
+        return
     line = {"metric": METRIC, "value": value, "unit": "s/RHS", "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000 * sum(x["t_solve"] for x in samples) / len(samples), "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": wl.describe(),
-            "cpu_baseline": {"value": value, "unit": "s/RHS", "cores": s["cores"], "kind": "oracle", "sample": sample},
+            "ms_per_step": 1000 * sum(times) / len(times), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": wl.describe(N),
+            "cpu_baseline": {"value": value, "unit": "s/RHS", "cores": ref.cores, "kind": "oracle", "sample": sample,
+                             "s_per_iteration_measured": per, "iterations": iters, "iterations_source": src,
+                             "projected": not full, "setup_s": ref.t_setup},
             "e2e": {"value": value, "unit": "s/RHS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------
+def apply_bandwidth(h, hbm, peak_src, log):
+    """Single right-hand side cpm_apply on the bumpy sphere band (K = 16 seeded
+    Gaussian bumps, Newton closest points): FP32 GB/s against HBM and FP64."""
+    import torch
+    import cpm_inputs as ci
+    from paper_2305_04711_gb300.cpm import Band
+    band = Band(ci.bumpy_sphere(16, seed=0), h).set_boundary([])
+    log(f"apply band N={band.N}")
+    out = {"workload": f"bumpy sphere (16 bumps, seed 0), h=1/{round(1 / h)}, no interior boundary",
+           "rows": band.NS}
+    for dt, bytes_row, key in ((torch.float32, BYTES_ROW_FP32, "fp32"), (torch.float64, BYTES_ROW_FP64, "fp64")):
+        u = torch.rand(band.N, dtype=dt, device="cuda")
+        v = torch.empty_like(u)
+        for _ in range(5):
+            band.apply(0.0, 1.0, u, out=v)
+        band.profile(True)
+        for _ in range(30):
+            band.apply(0.0, 1.0, u, out=v)
+        p = band.profile(False)
+        tms = p["apply_ms"] / p["applies"]
+        gbs = bytes_row * band.NS / (tms * 1e-3) / 1e9
+        out[key] = {"ms": tms, "GB/s_algorithmic": gbs, "hbm_peak_GB/s": hbm, "frac": gbs / hbm,
+                    "peak_source": peak_src, "bytes_per_row": bytes_row,
+                    "launches_per_product": p["launches"] / max(p["applies"], 1)}
+        if key == "fp64":
+            out[key]["TFLOP/s"] = FLOPS_ROW_FP64 * band.NS / (tms * 1e-3) / 1e12
+        del u, v
+    band.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -301,18 +405,18 @@ def run_ours(args):
 
     wl = Workload(args.workload, args.h)
     band = Band(wl.w.shape, wl.h).set_boundary(wl.w.curves, n_samples=wl.n_samples)
+    band.reserve(NRHS, fp32_ir=True)
     log(f"band N={band.N} (NS={band.NS}, NC={band.NC})")
-    s_host, g_host = wl.host_inputs(band)
-    if args.workload == "torus":
-        h_in = torch.tensor(wl.g, dtype=torch.float64).contiguous()   # [8][64] samples
+    _, cp_d = band.export_band()
+    cp = cp_d.cpu().numpy()
+    cpc = band.export_boundary()["cpc"].cpu().numpy()
+    h_in = torch.tensor(wl.host_inputs(band.NS, band.NC, cp, cpc), dtype=torch.float64).contiguous()
 
-        def make_rhs(dev_in):
+    def make_rhs(dev_in):
+        if wl.kind == "torus":
             return band.rhs(samples=dev_in, nrhs=NRHS)
-    else:
-        h_in = torch.tensor(np.concatenate([s_host, g_host], axis=0), dtype=torch.float64).contiguous()
+        return band.rhs(s=dev_in[:band.NS].contiguous(), g=dev_in[band.NS:].contiguous(), nrhs=NRHS)
 
-        def make_rhs(dev_in):
-            return band.rhs(s=dev_in[:band.NS].contiguous(), g=dev_in[band.NS:].contiguous(), nrhs=NRHS)
     d_in = h_in.to("cuda")
     F = make_rhs(d_in)
 
@@ -321,17 +425,17 @@ def run_ours(args):
         if dist:
             torch.distributed.barrier()
 
-    def step(fb):
-        return band.solve(0.0, 1.0, fb, tol=TOL, mode="fp32_ir", maxit=args.maxit, raise_on_error=False)
+    def step(fb, maxit=None):
+        return band.solve(0.0, 1.0, fb, tol=TOL, mode="fp32_ir", maxit=maxit or args.maxit, raise_on_error=False)
 
-    stats = []
+    # warm-up: the same solve, capped (graphs captured, caches and clocks warm)
     for k in range(args.warmup):
         t0 = time.perf_counter()
-        x, st = step(F)
+        x, st = step(F, args.warmup_maxit or None)
         torch.cuda.synchronize()
-        stats.append(st)
         log(f"warmup {k}: {time.perf_counter() - t0:.2f} s {st}")
     barrier()
+    stats = []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     band.profile(True)
     with Clocks(local) as clk:
@@ -345,7 +449,6 @@ def run_ours(args):
     prof = band.profile(False)
     ms = max_over_ranks(ev0.elapsed_time(ev1))
     log(f"timed: {ms / args.steps:.1f} ms/step {stats[-1]}")
-    ms_per_step = ms / args.steps
     value = seconds_per_rhs(ms, args.steps, NRHS, world)
     clocks = clk.summary()
     hbm, sm_max, peak_src = peaks()
@@ -353,42 +456,46 @@ def run_ours(args):
     # e2e through host buffers: per step the inputs come from pinned host memory,
     # the right-hand sides are built and solved on the device, and the solution
     # goes back to pinned host memory
+    e2e_steps = 1  # one full solve through host buffers (each takes about a minute)
     h_pin = h_in.pin_memory()
     h_x = torch.empty((band.N, NRHS), dtype=torch.float64).pin_memory()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        d_in = h_pin.to("cuda", non_blocking=True)
-        fb = make_rhs(d_in)
-        x, st = step(fb)
-        h_x.copy_(x, non_blocking=True)
+    for _ in range(e2e_steps):
+        dd = h_pin.to("cuda", non_blocking=True)
+        fb = make_rhs(dd)
+        xe, ste = step(fb)
+        h_x.copy_(xe, non_blocking=True)
         torch.cuda.synchronize()
     barrier()
     e2e_s = time.perf_counter() - t0
-    log(f"e2e: {e2e_s / args.steps:.2f} s/step")
-    e2e = {"value": e2e_s / (args.steps * NRHS * world), "unit": "s/RHS",
+    e2e = {"value": e2e_s / (e2e_steps * NRHS * world), "unit": "s/RHS", "steps": e2e_steps,
            "h2d_bytes_per_step": int(h_pin.numel() * 8), "d2h_bytes_per_step": int(h_x.numel() * 8)}
+    del xe, fb, dd
 
     line = {"metric": METRIC, "value": value, "unit": "s/RHS", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (FP64 solution, residual and refinement)", "data": "synthetic",
             "config": wl.describe(band.N), "clocks": clocks, "e2e": e2e, "gpu_launches": int(prof["launches"])}
     if rank == 0:
         last = stats[-1]
         line["solve"] = {"iterations": last.iterations, "fp64_iterations": last.fp64_iterations,
-                         "refinements": last.refinements, "relres_max": last.relres, "status": last.status}
-        # roofline of the dominant kernel, the batched FP32 product: the products
-        # of the timed region mix it with the FP64 residual / finish products, so
-        # it is timed by its own event series right after the timed region, on the
-        # same band and batch width
-        step_mean_ms = prof["apply_ms"] / max(prof["applies"], 1)
-        peak_tf = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+                         "refinements": last.refinements, "relres_max": last.relres, "status": last.status,
+                         "warmup_maxit": args.warmup_maxit}
+        props = torch.cuda.get_device_properties(local)
+        nsm = props.multi_processor_count
+        # roofline of the dominant kernel, the batched FP32 product (cell gather,
+        # flipped-entry correction, warp-per-row combine), timed by its own event
+        # series right after the timed region on the same band and batch width
+        peak_tf = nsm * 128 * 2 * sm_max * 1e6 / 1e12
+        fl = flops_row_rhs_batched(NRHS)
         roof = {"bound": "alu", "achieved": None, "peak": peak_tf, "unit": "TFLOP/s", "frac": None,
-                "traffic": profiled_traffic(),
-                "kernel": f"batched FP32 operator product (gather_cells + correct + combine_batched), {NRHS} RHS",
-                "peak_source": f"FP32 lanes x SMs x 2 x max SM clock ({sm_max:.0f} MHz), derived",
+                "traffic": profiled_traffic("batched_product_torus256_64rhs.md"),
+                "kernel": f"batched FP32 operator product, {NRHS} RHS",
+                "flop_per_row_rhs": fl,
+                "peak_source": f"FP32 FMA: {nsm} SMs x 128 lanes x 2 flop x max SM clock {sm_max:.0f} MHz (derived)",
                 "products_share_of_step": prof["apply_ms"] / ms if ms > 0 else None,
-                "step_products": prof["applies"] // max(args.steps, 1), "step_mean_product_ms": step_mean_ms}
+                "step_products": prof["applies"] // max(args.steps, 1)}
         try:
             u32 = torch.rand((band.N, NRHS), dtype=torch.float32, device="cuda")
             v32 = torch.empty_like(u32)
@@ -399,22 +506,17 @@ def run_ours(args):
                 band.apply(0.0, 1.0, u32, out=v32)
             p2 = band.profile(False)
             per_ms = p2["apply_ms"] / p2["applies"]
-            achieved_tf = FLOPS_ROW_RHS_FP32 * band.NS * NRHS / (per_ms * 1e-3) / 1e12
+            achieved_tf = fl * band.NS * NRHS / (per_ms * 1e-3) / 1e12
             roof.update({"achieved": achieved_tf, "frac": achieved_tf / peak_tf, "launch_ms": per_ms,
                          "launches": p2["applies"]})
             del u32, v32
         except Exception as e:  # reported, not required
             roof["error"] = str(e)
         line["roofline"] = roof
-        # accuracy of the batched result against the exact solutions (sphere)
-        if args.workload == "sphere":
-            a = band.extend(x)
-            errs = []
-            for k in (0, NRHS // 2, NRHS - 1):
-                ex = torch.tensor(wl.exact(band, k), device="cuda")
-                errs.append((a[:, k] - ex).abs().max().item())
-            line["surface_error_linf_vs_exact"] = max(errs)
-        # single right-hand side: FP64 solve (the comparison) and product bandwidth
+        # accuracy: against the closed form, and FP32+refinement against FP64
+        a = band.extend(x).cpu().numpy()
+        errs = [float(np.max(np.abs(a[:, k] - wl.exact(cp, k)))) for k in (0, NRHS // 2, NRHS - 1)]
+        line["surface_error_linf_vs_closed_form"] = max(errs)
         f0 = F[:, 0].contiguous()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -425,36 +527,47 @@ def run_ours(args):
         line["fp64_single"] = {"s_per_rhs": e0.elapsed_time(e1) / 1000.0, "iterations": st64.iterations,
                                "relres": st64.relres, "status": st64.status}
         log(f"fp64 single: {line['fp64_single']}")
-        diff = (x[:, 0] - x64).abs().max().item() / max(x64.abs().max().item(), 1e-300)
-        line["fp32ir_vs_fp64_rel_linf"] = diff
-        for dt, bytes_row, key in ((torch.float32, BYTES_ROW_FP32, "apply_fp32"),
-                                   (torch.float64, BYTES_ROW_FP64, "apply_fp64")):
-            u = torch.rand(band.N, dtype=dt, device="cuda")
-            v = torch.empty_like(u)
-            for _ in range(3):
-                band.apply(0.0, 1.0, u, out=v)
-            band.profile(True)
-            for _ in range(20):
-                band.apply(0.0, 1.0, u, out=v)
-            p1 = band.profile(False)
-            tms = p1["apply_ms"] / p1["applies"]
-            gbs = bytes_row * band.NS / (tms * 1e-3) / 1e9
-            line[key] = {"ms": tms, "GB/s_algorithmic": gbs, "hbm_peak_GB/s": hbm, "frac": gbs / hbm,
-                         "peak_source": peak_src, "rows": band.NS}
+        line["fp32ir_vs_fp64_rel_linf"] = (x[:, 0] - x64).abs().max().item() / max(x64.abs().max().item(), 1e-300)
+        if args.fp64_batch:
+            e0.record()
+            xb, stb = band.solve(0.0, 1.0, F, tol=TOL, mode="fp64", maxit=args.maxit, raise_on_error=False)
+            e1.record()
+            torch.cuda.synchronize()
+            line["fp64_batch"] = {"s_per_rhs": e0.elapsed_time(e1) / 1000.0 / NRHS, "iterations": stb.iterations,
+                                  "relres_max": stb.relres, "status": stb.status,
+                                  "fp32ir_vs_fp64_rel_linf": ((x - xb).abs().max() / xb.abs().max()).item()}
+            del xb
+        del x
+        if args.apply_h > 0:
+            band.close()
+            del F, d_in
+            torch.cuda.empty_cache()
+            try:
+                line["apply_bumpy"] = apply_bandwidth(args.apply_h, hbm, peak_src, log)
+            except Exception as e:
+                line["apply_bumpy"] = {"error": str(e)}
         if not args.no_cpu_baseline and world == 1:
             try:
-                s = cpu_baseline_sample(args.workload)
-                value_cpu = s["s_per_dof_iter"] * band.N * st64.iterations
+                ref = OracleSample(wl)
+                n_it = args.cpu_iters or (4 if ref.o.N > 2_000_000 else 16)
+                per = ref.time_iterations(n_it)
+                gold = golden_iterations(wl)
+                if gold is not None:
+                    iters, src = gold["iterations"], "the oracle's own solve (recorded)"
+                else:
+                    iters, src = st64.iterations, "the GPU FP64 solve (same BiCGSTAB, preconditioner and test)"
                 line["cpu_baseline"] = {
-                    "value": value_cpu, "unit": "s/RHS", "cores": s["cores"], "kind": "oracle",
-                    "sample": f"oracle BiCGSTAB solve of 1 RHS on the same geometry at h=1/{round(1 / s['h'])} "
-                              f"({s['N']} DOF, {s['iters']} iterations, {s['t_solve']:.1f} s); time per "
-                              f"DOF-iteration x {band.N} DOF x {st64.iterations} iterations (the GPU FP64 count)"}
+                    "value": per * iters, "unit": "s/RHS", "cores": ref.cores, "kind": "oracle",
+                    "sample": (f"{n_it} oracle BiCGSTAB iterations on the same band ({ref.o.N} DOF) and right-hand "
+                               f"side, timed ({per:.3f} s/iteration), x {iters} iterations from {src}; projected"),
+                    "s_per_iteration_measured": per, "iterations": iters, "iterations_source": src,
+                    "projected": True, "setup_s": ref.t_setup}
             except Exception as e:  # the baseline is reported, not required
                 line["cpu_baseline"] = {"value": None, "unit": "s/RHS", "cores": None, "kind": "oracle",
                                         "sample": f"failed: {e}"}
         print(json.dumps(line), flush=True)
-    band.close()
+    else:
+        band.close()
     if dist:
         torch.distributed.destroy_process_group()
 

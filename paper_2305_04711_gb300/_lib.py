@@ -17,13 +17,15 @@ STATUS = {0: "CPM_OK", 1: "CPM_ERR_ARG", 2: "CPM_ERR_OOM", 3: "CPM_ERR_CUDA", 4:
           9: "CPM_ERR_TIMEOUT", 10: "CPM_ERR_STATE"}
 PREC_FP64, PREC_FP32 = 0, 1
 SOLVE_FP64, SOLVE_FP32_IR = 0, 1
-NORM_SCALED, NORM_PLAIN = 0, 1
+NORM_PLAIN, NORM_SCALED = 0, 1
+RESERVE_FP64, RESERVE_FP32_IR = 1, 2
 
 # every entry point that include/cpm.h declares
 EXPORTS = ["cpm_band_build", "cpm_band_info", "cpm_export_band", "cpm_set_boundary", "cpm_export_boundary",
            "cpm_rhs", "cpm_apply", "cpm_apply_transpose", "cpm_extend", "cpm_solve", "cpm_solve_adjoint",
            "cpm_boundary_grad", "cpm_destroy", "cpm_status_str", "cpm_diagnostics", "cpm_profile",
-           "cpm_apply_noalloc", "cpm_apply_noalloc_max_bytes", "cpm_surface_gradient", "cpm_surface_divergence"]
+           "cpm_apply_noalloc", "cpm_apply_noalloc_max_bytes", "cpm_surface_gradient", "cpm_surface_divergence",
+           "cpm_reserve", "cpm_autotune", "cpm_set_tune"]
 
 
 class ShapeDesc(ctypes.Structure):
@@ -36,7 +38,7 @@ class ShapeDesc(ctypes.Structure):
 class CurveDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("bc", ctypes.c_int), ("p", ctypes.c_double * 3),
                 ("nu", ctypes.c_double * 3), ("rad", ctypes.c_double), ("ref", ctypes.c_double * 3),
-                ("two_sided", ctypes.c_int), ("n_samples", ctypes.c_int)]
+                ("two_sided", ctypes.c_int), ("n_samples", ctypes.c_int), ("bc_minus", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -45,9 +47,18 @@ class SolveOpts(ctypes.Structure):
                 ("norm", ctypes.c_int), ("inner_maxit", ctypes.c_int)]
 
 
+class TuneInfo(ctypes.Structure):
+    _fields_ = [("cells_xh", ctypes.c_int), ("cells_blocks_per_sm", ctypes.c_int),
+                ("combine_warps_per_sm", ctypes.c_int), ("vec_blocks_per_sm", ctypes.c_int),
+                ("gather1_per_cell", ctypes.c_int),
+                ("product_ms", ctypes.c_double), ("product_ms_default", ctypes.c_double),
+                ("vector_ms", ctypes.c_double)]
+
+
 class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int), ("restarts", ctypes.c_int),
-                ("relres", ctypes.c_double), ("status", ctypes.c_int), ("fp64_iterations", ctypes.c_int)]
+                ("relres", ctypes.c_double), ("status", ctypes.c_int), ("fp64_iterations", ctypes.c_int),
+                ("relres_floor", ctypes.c_double)]
 
 
 _lib = None
@@ -63,11 +74,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L = ctypes.CDLL(path)
     P, d, i, i64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64
     pi64 = ctypes.POINTER(i64)
-    L.cpm_band_build.argtypes = [ctypes.POINTER(ShapeDesc), d, d, P, ctypes.POINTER(P)]
+    L.cpm_band_build.argtypes = [ctypes.POINTER(ShapeDesc), d, i, d, P, ctypes.POINTER(P)]
     L.cpm_band_info.argtypes = [P, pi64, pi64, ctypes.POINTER(d), pi64]
     L.cpm_export_band.argtypes = [P, P, P, P]
     L.cpm_set_boundary.argtypes = [P, ctypes.POINTER(CurveDesc), i]
-    L.cpm_export_boundary.argtypes = [P, P, P, P, P, P, P]
+    L.cpm_export_boundary.argtypes = [P, P, P, P, P, P, P, P]
     L.cpm_rhs.argtypes = [P, P, P, P, P, i, i64, P]
     L.cpm_apply.argtypes = [P, d, d, i, P, P, i, i64, P]
     L.cpm_apply_transpose.argtypes = [P, d, d, i, P, P, i, i64, P]
@@ -86,6 +97,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.cpm_status_str.restype = ctypes.c_char_p
     L.cpm_diagnostics.argtypes = [P, pi64, pi64]
     L.cpm_profile.argtypes = [P, i, ctypes.POINTER(d), pi64, pi64, pi64]
+    L.cpm_reserve.argtypes = [P, i64, i]
+    L.cpm_autotune.argtypes = [P, i, i64, i, ctypes.POINTER(TuneInfo), P]
+    L.cpm_set_tune.argtypes = [P, i, i, ctypes.POINTER(TuneInfo)]
     for name in EXPORTS:
         if name not in ("cpm_destroy", "cpm_status_str", "cpm_apply_noalloc_max_bytes"):
             getattr(L, name).restype = ctypes.c_int

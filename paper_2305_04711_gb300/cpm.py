@@ -51,6 +51,7 @@ class SolveStats:
     relres: float
     status: str
     fp64_iterations: int = 0
+    relres_floor: float = 0.0
 
 
 def shape_desc(shape) -> tuple:
@@ -85,19 +86,21 @@ def curve_descs(curves: Sequence, n_samples: Optional[Sequence[int]] = None):
         c.rad = float(cv.rad)
         c.two_sided = int(bool(getattr(cv, "two_sided", False)))
         c.n_samples = int(n_samples[i]) if n_samples is not None else 1
+        c.bc_minus = int(getattr(cv, "bc_minus", 0) or 0)
     return arr
 
 
 class Band:
     """A band Omega(S) with its operator (one cpm_ctx)."""
 
-    def __init__(self, shape, h: float, r_band: float = -1.0):
+    def __init__(self, shape, h: float, r_band: float = -1.0, p: int = 3):
         self._lib = L.load()
         self._h = ctypes.c_void_p()
         d, keep = shape_desc(shape)
-        L.check(self._lib.cpm_band_build(ctypes.byref(d), float(h), float(r_band), _stream(), ctypes.byref(self._h)),
-                "cpm_band_build")
+        L.check(self._lib.cpm_band_build(ctypes.byref(d), float(h), int(p), float(r_band), _stream(),
+                                         ctypes.byref(self._h)), "cpm_band_build")
         self.h = float(h)
+        self.p = int(p)
         self.dim = int(shape.dim)
         self._sizes()
         self.n_samples = []
@@ -138,6 +141,19 @@ class Band:
         self.n_samples = list(n_samples) if n_samples is not None else [1] * len(curves)
         self.curves = list(curves)
         self._sizes()
+        self._reserved = (1, L.RESERVE_FP64 | L.RESERVE_FP32_IR)  # what cpm_set_boundary reserves
+        return self
+
+    def reserve(self, ld: int, fp32_ir: bool = True):
+        """cpm_reserve: workspaces for leading dimension `ld` (products, and the
+        FP64 and, with fp32_ir, FP32+refinement solves).  The calls below reserve
+        on demand; calling this first keeps the allocation out of timed work."""
+        flags = L.RESERVE_FP64 | (L.RESERVE_FP32_IR if fp32_ir else 0)
+        ld0, f0 = getattr(self, "_reserved", (0, 0))
+        if ld <= ld0 and (f0 | flags) == f0:
+            return self
+        L.check(self._lib.cpm_reserve(self._h, int(max(ld, ld0)), int(f0 | flags)), "cpm_reserve")
+        self._reserved = (max(ld, ld0), f0 | flags)
         return self
 
     def export_boundary(self):
@@ -147,10 +163,12 @@ class Band:
         cpc = torch.empty((n, 3), dtype=torch.float64, device="cuda")
         side = torch.empty(n, dtype=torch.int32, device="cuda")
         param = torch.empty(n, dtype=torch.float64, device="cuda")
+        btype = torch.empty(n, dtype=torch.int32, device="cuda")
         L.check(self._lib.cpm_export_boundary(self._h, _ptr(twin), _ptr(curve), _ptr(cpc), _ptr(side), _ptr(param),
-                                              _stream()), "cpm_export_boundary")
+                                              _ptr(btype), _stream()), "cpm_export_boundary")
         k = self.NC
-        return {"twin": twin[:k], "curve": curve[:k], "cpc": cpc[:k], "side": side[:k], "param": param[:k]}
+        return {"twin": twin[:k], "curve": curve[:k], "cpc": cpc[:k], "side": side[:k], "param": param[:k],
+                "type": btype[:k]}
 
     def profile(self, enable: bool):
         """Start (True) or stop (False) the library's product timing; stopping
@@ -160,6 +178,26 @@ class Band:
                                       ctypes.byref(launches), ctypes.byref(rr)), "cpm_profile")
         return None if enable else {"apply_ms": ms.value, "applies": calls.value, "launches": launches.value,
                                     "row_rhs": rr.value}
+
+    def autotune(self, nrhs: int, dtype=torch.float32) -> dict:
+        """cpm_autotune: time the launch-shape candidates for nrhs columns of
+        dtype on this band and keep the fastest; returns the choices."""
+        prec = {torch.float64: L.PREC_FP64, torch.float32: L.PREC_FP32}[dtype]
+        self.reserve(nrhs, fp32_ir=(dtype == torch.float32))
+        info = L.TuneInfo()
+        L.check(self._lib.cpm_autotune(self._h, int(nrhs), int(nrhs), prec, ctypes.byref(info), _stream()),
+                "cpm_autotune")
+        return {k: getattr(info, k) for k, _ in L.TuneInfo._fields_}
+
+    def set_tune(self, nrhs: int, dtype=torch.float32, **shapes) -> "Band":
+        """cpm_set_tune: fix the launch shapes (the keys of autotune's report;
+        a missing key or 0 is the default)."""
+        prec = L.PREC_FP32 if dtype == torch.float32 else L.PREC_FP64
+        info = L.TuneInfo()
+        for k, v in shapes.items():
+            setattr(info, k, v)
+        L.check(self._lib.cpm_set_tune(self._h, int(nrhs), prec, ctypes.byref(info)), "cpm_set_tune")
+        return self
 
     def diagnostics(self):
         a, b = ctypes.c_int64(), ctypes.c_int64()
@@ -180,6 +218,7 @@ class Band:
         nrhs, ld = _layout(u, self.N)
         prec = {torch.float64: L.PREC_FP64, torch.float32: L.PREC_FP32}[u.dtype]
         v = torch.empty_like(u) if out is None else out
+        self.reserve(ld, fp32_ir=False)
         fn = self._lib.cpm_apply_transpose if transpose else self._lib.cpm_apply
         L.check(fn(self._h, float(m), float(n), prec, _ptr(u), _ptr(v), nrhs, ld, _stream()),
                 "cpm_apply_transpose" if transpose else "cpm_apply")
@@ -197,6 +236,7 @@ class Band:
     def extend(self, u: torch.Tensor) -> torch.Tensor:
         nrhs, ld = _layout(u, self.N)
         a = torch.empty((self.NS,) if nrhs == 1 else (self.NS, nrhs), dtype=torch.float64, device="cuda")
+        self.reserve(max(ld, nrhs), fp32_ir=False)
         L.check(self._lib.cpm_extend(self._h, _ptr(u), _ptr(a), nrhs, ld, _stream()), "cpm_extend")
         return a
 
@@ -219,9 +259,10 @@ class Band:
 
     def solve(self, m: float, n: float, f: torch.Tensor, x0: Optional[torch.Tensor] = None, tol: float = 1e-10,
               maxit: int = 20000, mode: str = "fp64", inner_tol: float = 0.0, max_refine: int = 0,
-              check_every: int = 16, adjoint: bool = False, raise_on_error: bool = True, norm: str = "scaled",
+              check_every: int = 16, adjoint: bool = False, raise_on_error: bool = True, norm: str = "plain",
               inner_maxit: int = 0):
         nrhs, ld = _layout(f, self.N)
+        self.reserve(ld, fp32_ir=(mode != "fp64"))
         x = torch.zeros_like(f) if x0 is None else x0.clone()
         o = L.SolveOpts(tol, maxit, L.SOLVE_FP64 if mode == "fp64" else L.SOLVE_FP32_IR, inner_tol, max_refine,
                         check_every, L.NORM_SCALED if norm == "scaled" else L.NORM_PLAIN, inner_maxit)
@@ -230,7 +271,7 @@ class Band:
         rc = fn(self._h, float(m), float(n), _ptr(f), _ptr(x), nrhs, ld, ctypes.byref(o), ctypes.byref(st),
                 _stream())
         stats = SolveStats(st.iterations, st.refinements, st.restarts, st.relres, L.STATUS.get(rc, str(rc)),
-                           st.fp64_iterations)
+                           st.fp64_iterations, st.relres_floor)
         if raise_on_error:
             L.check(rc, "cpm_solve_adjoint" if adjoint else "cpm_solve")
         return x, stats

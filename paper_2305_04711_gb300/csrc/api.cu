@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" entry points declared in include/cpm.h.
 // Argument checking and status mapping live here; the work is in band.cu,
 // boundary.cu, apply.cu, transpose.cu and krylov.cu.
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -32,6 +33,7 @@ const char *cpm_status_str(cpm_status s) {
 void cpm_destroy(cpm_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->istream) cudaStreamSynchronize(c->istream);
   cpm_free_solve(c);
   cpm_free_boundary(c);
   cpm_internal_free_band(c);
@@ -39,17 +41,20 @@ void cpm_destroy(cpm_ctx *c) {
   cudaFree(c->d_shape_c);
   cudaFree(c->a_scratch.p);
   cudaFree(c->b_scratch.p);
-  cudaFree(c->heat_scratch.p);
+  for (auto e : c->ev_join)
+    if (e) cudaEventDestroy(e);
+  if (c->istream) cudaStreamDestroy(c->istream);
   cudaFree(c->d_err);
   cudaFree(c->d_counter);
   for (auto e : c->prof.ev) cudaEventDestroy(e);
   delete c;
 }
 
-cpm_status cpm_band_build(const cpm_shape_desc *shape, double h, double r_band, void *stream, cpm_ctx **out) {
+cpm_status cpm_band_build(const cpm_shape_desc *shape, double h, int p, double r_band, void *stream,
+                          cpm_ctx **out) {
   if (!out) return CPM_ERR_ARG;
   *out = nullptr;
-  if (!shape || !(h > 0.0)) return CPM_ERR_ARG;
+  if (!shape || !(h > 0.0) || (p != 2 && p != 3)) return CPM_ERR_ARG;
   if (shape->kind < CPM_SHAPE_CIRCLE || shape->kind > CPM_SHAPE_BUMPY) return CPM_ERR_ARG;
   if ((shape->kind == CPM_SHAPE_CIRCLE) != (shape->dim == 2)) return CPM_ERR_ARG;
   if (shape->dim != 2 && shape->dim != 3) return CPM_ERR_ARG;
@@ -58,13 +63,17 @@ cpm_status cpm_band_build(const cpm_shape_desc *shape, double h, double r_band, 
   cpm_ctx *c = new (std::nothrow) cpm_ctx;
   if (!c) return CPM_ERR_OOM;
   c->stream = as_stream(stream);
+  c->nsm = cpm_device_sms();
   if (cudaMalloc(&c->d_err, sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&c->d_counter, sizeof(unsigned long long) * 4) != cudaSuccess) {
+      cudaMalloc(&c->d_counter, sizeof(unsigned long long) * 4) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->istream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join[1], cudaEventDisableTiming) != cudaSuccess) {
     (void)cudaGetLastError();
     cpm_destroy(c);
     return CPM_ERR_OOM;
   }
-  cpm_status rc = cpm_internal_band_build(c, shape, h, r_band);
+  cpm_status rc = cpm_internal_band_build(c, shape, h, p, r_band);
   if (rc != CPM_OK) {
     cpm_destroy(c);
     return rc;
@@ -95,17 +104,46 @@ cpm_status cpm_set_boundary(cpm_ctx *c, const cpm_curve_desc *curves, int n) {
   for (int k = 0; k < n; ++k) {
     const cpm_curve_desc &d = curves[k];
     if (d.kind != CPM_CURVE_POINT && d.kind != CPM_CURVE_CIRCLE) return CPM_ERR_ARG;
-    if (d.bc != CPM_BC_DIR1 && d.bc != CPM_BC_DIR2) return CPM_ERR_ARG;
+    if (d.bc < CPM_BC_DIR1 || d.bc > CPM_BC_NEU2) return CPM_ERR_ARG;
+    if (d.bc_minus < 0 || d.bc_minus > CPM_BC_NEU2) return CPM_ERR_ARG;
+    // a point in 3D has no sides, hence no conormal for a Neumann condition (Sec. 4.5)
+    const bool neu = d.bc >= CPM_BC_NEU1 || d.bc_minus >= CPM_BC_NEU1;
+    if (neu && d.kind == CPM_CURVE_POINT && c->dim == 3) return CPM_ERR_ARG;
     if (d.n_samples < 1) return CPM_ERR_ARG;
     if (d.kind == CPM_CURVE_POINT && d.n_samples != 1) return CPM_ERR_ARG;
     if (d.kind == CPM_CURVE_CIRCLE && !(d.rad > 0.0)) return CPM_ERR_ARG;
   }
   cpm_free_solve(c);
-  return cpm_internal_set_boundary(c, curves, n);
+  c->res_ld = 0;
+  c->res_flags = 0;
+  cpm_status rc = cpm_internal_set_boundary(c, curves, n);
+  if (rc) return rc;
+  // single right-hand side workspaces of every product and solve form
+  return cpm_reserve(c, 1, CPM_RESERVE_FP64 | CPM_RESERVE_FP32_IR);
+}
+
+cpm_status cpm_reserve(cpm_ctx *c, int64_t ld, int flags) {
+  if (!c || ld < 1 || ld > 256 || (flags & ~(CPM_RESERVE_FP64 | CPM_RESERVE_FP32_IR))) return CPM_ERR_ARG;
+  if (!c->boundary_set) return CPM_ERR_STATE;
+  // product intermediates: [N_S][ld] of the widest element (FP64), at least 3
+  // FP64 columns for the heat steps' vector extensions
+  const size_t scratch = sizeof(double) * (size_t)std::max<int64_t>(c->NS, 1) * (size_t)std::max<int64_t>(ld, 3);
+  const size_t bscr = sizeof(double) * (size_t)std::max<int64_t>(c->NS, 1) * (size_t)ld;
+  cpm_status rc = cpm_ensure(c->a_scratch, scratch);
+  if (rc) return rc;
+  rc = cpm_ensure(c->b_scratch, bscr);
+  if (rc) return rc;
+  if (flags) {
+    rc = cpm_reserve_solve(c, ld, (flags & CPM_RESERVE_FP32_IR) != 0);
+    if (rc) return rc;
+  }
+  c->res_ld = std::max(c->res_ld, ld);
+  c->res_flags |= flags;
+  return CPM_OK;
 }
 
 cpm_status cpm_export_boundary(const cpm_ctx *c, int64_t *twin, int32_t *curve, double *cpc, int32_t *side,
-                               double *param, void *stream) {
+                               double *param, int32_t *type, void *stream) {
   if (!c || !c->boundary_set) return c ? CPM_ERR_STATE : CPM_ERR_ARG;
   cudaStream_t st = as_stream(stream);
   if (c->NC == 0) return CPM_OK;
@@ -127,6 +165,7 @@ cpm_status cpm_export_boundary(const cpm_ctx *c, int64_t *twin, int32_t *curve, 
   if (cpc) CPM_CUDA_TRY(cudaMemcpyAsync(cpc, c->d_cpc, sizeof(double) * 3 * c->NC, cudaMemcpyDeviceToDevice, st));
   if (side) CPM_CUDA_TRY(cudaMemcpyAsync(side, c->d_side, sizeof(int32_t) * c->NC, cudaMemcpyDeviceToDevice, st));
   if (param) CPM_CUDA_TRY(cudaMemcpyAsync(param, c->d_param, sizeof(double) * c->NC, cudaMemcpyDeviceToDevice, st));
+  if (type) CPM_CUDA_TRY(cudaMemcpyAsync(type, c->d_bc_type, sizeof(int32_t) * c->NC, cudaMemcpyDeviceToDevice, st));
   return CPM_OK;
 }
 
@@ -251,6 +290,18 @@ cpm_status cpm_profile(cpm_ctx *c, int enable, double *apply_ms, int64_t *apply_
   if (row_rhs_processed) *row_rhs_processed = p.row_rhs;
   p.used = 0;
   return CPM_OK;
+}
+
+cpm_status cpm_autotune(cpm_ctx *c, int nrhs, int64_t ld, int prec, cpm_tune_info *info, void *stream) {
+  if (!c || bad_batch(nrhs, ld) || (prec != CPM_PREC_FP32 && prec != CPM_PREC_FP64)) return CPM_ERR_ARG;
+  if (!c->boundary_set) return CPM_ERR_STATE;
+  return cpm_internal_autotune(c, nrhs, ld, prec, info, as_stream(stream));
+}
+
+cpm_status cpm_set_tune(cpm_ctx *c, int nrhs, int prec, const cpm_tune_info *t) {
+  if (!c || !t || nrhs < 1 || (prec != CPM_PREC_FP32 && prec != CPM_PREC_FP64)) return CPM_ERR_ARG;
+  if (!c->boundary_set) return CPM_ERR_STATE;
+  return cpm_internal_set_tune(c, nrhs, prec, t);
 }
 
 cpm_status cpm_diagnostics(const cpm_ctx *c, int64_t *noflip, int64_t *nspec) {

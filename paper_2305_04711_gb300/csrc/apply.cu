@@ -21,14 +21,15 @@
 
 namespace {
 
-template <typename T, bool DIFF>
-__device__ __forceinline__ T line4(const T *u, int64_t ld, int r, int32_t s0, int32_t s1, int split, const T w[4],
-                                   T ui) {
-  // nodes 0..split-1 are consecutive from s0, nodes split..3 consecutive from s1;
-  // a negative start (a node outside the band, excluded at set-up) reads nothing
+template <typename T, bool DIFF, int NP>
+__device__ __forceinline__ T line_sum(const T *u, int64_t ld, int r, int32_t s0, int32_t s1, int split, const T *w,
+                                      T ui) {
+  // nodes 0..split-1 are consecutive from s0, nodes split..NP-1 consecutive from
+  // s1; a negative start (a node outside the band, excluded at set-up) reads
+  // nothing
   T acc = T(0);
 #pragma unroll
-  for (int cx = 0; cx < 4; ++cx) {
+  for (int cx = 0; cx < NP; ++cx) {
     int32_t st = (cx < split) ? s0 : s1;
     int32_t idx = (cx < split) ? (s0 + cx) : (s1 + (cx - split));
     if (st >= 0) {
@@ -43,9 +44,12 @@ __device__ __forceinline__ T line4(const T *u, int64_t ld, int r, int32_t s0, in
 // sum_j w_j u_j.  Subtracting neighbouring values first keeps the rounding
 // error relative to the differences (exact when close, Sterbenz), which FP32
 // needs on smooth fields where the Laplacian cancels O(1) values to O(h^2).
-template <typename T, bool DIFF>
-__global__ void __launch_bounds__(256) gather_kernel(ApplyArgs<T> A, const T *__restrict__ u, T *__restrict__ a,
-                                                     int nrhs, int64_t ld) {
+// cs scales the values of PDE DOFs on input (a right diagonal factor C: the
+// product is then E C u); BC DOFs enter unscaled.
+template <typename T, bool DIFF, int NP>
+__global__ void __launch_bounds__(256) gather_kernel(ApplyArgs<T> A, T cs, const T *__restrict__ u,
+                                                     T *__restrict__ a, int nrhs, int64_t ld) {
+  const int64_t NS = A.v.NS;
   CPM_ROWS_COLS_LOOP(A.v.NS, nrhs, i, r) {
     uint32_t rb = __ldg(A.rbase + i);
     T acc = T(0);
@@ -57,8 +61,8 @@ __global__ void __launch_bounds__(256) gather_kernel(ApplyArgs<T> A, const T *__
       for (int e = 0; e < 64; ++e) {
         int32_t c = __ldg(ec + e);
         if (c >= 0) {
-          T val = __ldg(u + (int64_t)c * ld + r);
-          acc += __ldg(ew + e) * (DIFF ? (val - ui) : val);
+          const T val = __ldg(u + (int64_t)c * ld + r) * ((c < NS) ? cs : T(1));
+          acc += __ldg(ew + e) * (DIFF ? (val - cs * ui) : val);
         }
       }
     } else {
@@ -66,22 +70,23 @@ __global__ void __launch_bounds__(256) gather_kernel(ApplyArgs<T> A, const T *__
       int l = (int)(rb & 511u);
       int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
       T wx[4], wy[4], wz[4];
-      cpm_lagrange4<T>(__ldg(A.t + 3 * i), wx);
-      cpm_lagrange4<T>(__ldg(A.t + 3 * i + 1), wy);
-      const int nz = (A.v.dim == 3) ? 4 : 1;
-      if (A.v.dim == 3) cpm_lagrange4<T>(__ldg(A.t + 3 * i + 2), wz);
+      cpm_lagrange<NP, T>(__ldg(A.t + 3 * i), wx);
+      cpm_lagrange<NP, T>(__ldg(A.t + 3 * i + 1), wy);
+      const int nz = (A.v.dim == 3) ? NP : 1;
+      if (A.v.dim == 3) cpm_lagrange<NP, T>(__ldg(A.t + 3 * i + 2), wz);
       else { wz[0] = T(1); wz[1] = wz[2] = wz[3] = T(0); }
-      const int split = (lx + 3 < 8) ? 4 : 8 - lx;
+      const int split = (lx + NP - 1 < 8) ? NP : 8 - lx;
       for (int cz = 0; cz < nz; ++cz) {
         T pz = T(0);
 #pragma unroll
-        for (int cy = 0; cy < 4; ++cy) {
+        for (int cy = 0; cy < NP; ++cy) {
           int32_t s0 = cpm_node_index(A.v, b, lx, ly + cy, lz + cz);
-          int32_t s1 = (split < 4) ? cpm_node_index(A.v, b, 8, ly + cy, lz + cz) : 0;
-          pz += wy[cy] * line4<T, DIFF>(u, ld, r, s0, s1, split, wx, ui);
+          int32_t s1 = (split < NP) ? cpm_node_index(A.v, b, 8, ly + cy, lz + cz) : 0;
+          pz += wy[cy] * line_sum<T, DIFF, NP>(u, ld, r, s0, s1, split, wx, ui);
         }
         acc += wz[cz] * pz;
       }
+      acc *= cs;
     }
     a[i * ld + r] = acc;
   }
@@ -91,9 +96,9 @@ __global__ void __launch_bounds__(256) gather_kernel(ApplyArgs<T> A, const T *__
 // m u_i + (n/h^2) [ sum_present (a_k + (u_k - u_i)) - n_missing u_i ],
 // the same value as m u_i + n [diag(L) u_i + (1/h^2) sum_present (E u)_k].
 template <typename T, bool DIFF>
-__global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, T rowscale, const T *__restrict__ u,
-                                                      const T *__restrict__ a, T *__restrict__ v, int nrhs,
-                                                      int64_t ld) {
+__global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, T rowscale, T cs,
+                                                      const T *__restrict__ u, const T *__restrict__ a,
+                                                      T *__restrict__ v, int nrhs, int64_t ld) {
   const int64_t NS = A.v.NS, N = NS + A.v.NC;
   const T inv_h2 = T(A.v.inv_h * A.v.inv_h);
   const T diag = m + n * T(-2.0 * A.v.dim * A.v.inv_h * A.v.inv_h);
@@ -101,7 +106,7 @@ __global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, 
   CPM_ROWS_COLS_LOOP(N, nrhs, i, r) {
     if (i < NS) {
       uint32_t rb = __ldg(A.rbase + i);
-      const T ui = __ldg(u + i * ld + r);
+      const T ui = cs * __ldg(u + i * ld + r);
       T s = T(0);
       int present = 0;
       if (A.nbr8) {
@@ -116,7 +121,7 @@ __global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, 
           ++present;
           if (c < NS) {
             const T ac = __ldg(a + (int64_t)c * ld + r);
-            s += DIFF ? ac + (__ldg(u + (int64_t)c * ld + r) - ui) : ac;
+            s += DIFF ? ac + (cs * __ldg(u + (int64_t)c * ld + r) - ui) : ac;
           } else {
             const T uc = __ldg(u + (int64_t)c * ld + r);
             s += DIFF ? (uc - ui) : uc;
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, 
           int32_t c = __ldg(A.fcol + sp * 6 + k);
           if (c < 0) continue;
           ++present;
-          T uc = __ldg(u + (int64_t)c * ld + r);
+          const T uc = __ldg(u + (int64_t)c * ld + r) * ((c < NS) ? cs : T(1));
           if (DIFF) s += (c < NS) ? (__ldg(a + (int64_t)c * ld + r) + (uc - ui)) : (uc - ui);
           else s += (c < NS) ? __ldg(a + (int64_t)c * ld + r) : uc;
         }
@@ -150,7 +155,7 @@ __global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, 
           if (j < 0) continue;
           ++present;
           T aj = __ldg(a + (int64_t)j * ld + r);
-          if (DIFF) s += aj + (__ldg(u + (int64_t)j * ld + r) - ui);
+          if (DIFF) s += aj + (cs * __ldg(u + (int64_t)j * ld + r) - ui);
           else s += aj;
         }
       }
@@ -162,8 +167,10 @@ __global__ void __launch_bounds__(256) combine_kernel(ApplyArgs<T> A, T m, T n, 
       int64_t al = i - NS;
       int cnt = __ldg(A.bc_cnt + al);
       T s = T(0);
-      for (int e = 0; e < cnt; ++e)
-        s += __ldg(A.bc_val + al * CPM_BC_STRIDE + e) * __ldg(u + (int64_t)__ldg(A.bc_col + al * CPM_BC_STRIDE + e) * ld + r);
+      for (int e = 0; e < cnt; ++e) {
+        const int32_t c = __ldg(A.bc_col + al * CPM_BC_STRIDE + e);
+        s += __ldg(A.bc_val + al * CPM_BC_STRIDE + e) * (__ldg(u + (int64_t)c * ld + r) * ((c < NS) ? cs : T(1)));
+      }
       v[i * ld + r] = s;
     }
   }
@@ -203,7 +210,7 @@ __device__ __forceinline__ void stv(T *p, const T in[RPL]) {
 }
 
 template <typename T, bool DIFF, int RPL>
-__global__ void __launch_bounds__(256) combine_batched_kernel(ApplyArgs<T> A, T m, T n, T rowscale,
+__global__ void __launch_bounds__(256) combine_batched_kernel(ApplyArgs<T> A, T m, T n, T rowscale, T cs,
                                                               const T *__restrict__ u, const T *__restrict__ a,
                                                               T *__restrict__ v, int nrhs, int64_t ld) {
   const int lane = threadIdx.x & 31;
@@ -243,7 +250,10 @@ __global__ void __launch_bounds__(256) combine_batched_kernel(ApplyArgs<T> A, T 
       T ui[RPL], s[RPL];
       ldv<T, RPL>(u + i * ld + col, ui);
 #pragma unroll
-      for (int k = 0; k < RPL; ++k) s[k] = T(0);
+      for (int k = 0; k < RPL; ++k) {
+        ui[k] *= cs;
+        s[k] = T(0);
+      }
       int present = 0;
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
@@ -253,8 +263,10 @@ __global__ void __launch_bounds__(256) combine_batched_kernel(ApplyArgs<T> A, T 
         T uc[RPL], ac[RPL];
         if (DIFF || c >= NS) ldv<T, RPL>(u + (int64_t)c * ld + col, uc);
         if (c < NS) ldv<T, RPL>(a + (int64_t)c * ld + col, ac);
+        const T sc_c = (c < NS) ? cs : T(1);
 #pragma unroll
         for (int k = 0; k < RPL; ++k) {
+          uc[k] *= sc_c;
           if (DIFF) s[k] += (c < NS) ? (ac[k] + (uc[k] - ui[k])) : (uc[k] - ui[k]);
           else s[k] += (c < NS) ? ac[k] : uc[k];
         }
@@ -272,8 +284,10 @@ __global__ void __launch_bounds__(256) combine_batched_kernel(ApplyArgs<T> A, T 
 #pragma unroll
       for (int k = 0; k < RPL; ++k) out[k] = T(0);
       for (int e = 0; e < cnt; ++e) {
-        T w = __ldg(A.bc_val + al * CPM_BC_STRIDE + e), val[RPL];
-        ldv<T, RPL>(u + (int64_t)__ldg(A.bc_col + al * CPM_BC_STRIDE + e) * ld + col, val);
+        const int32_t cc = __ldg(A.bc_col + al * CPM_BC_STRIDE + e);
+        const T w = __ldg(A.bc_val + al * CPM_BC_STRIDE + e) * ((cc < NS) ? cs : T(1));
+        T val[RPL];
+        ldv<T, RPL>(u + (int64_t)cc * ld + col, val);
 #pragma unroll
         for (int k = 0; k < RPL; ++k) out[k] += w * val[k];
       }
@@ -285,20 +299,21 @@ __global__ void __launch_bounds__(256) combine_batched_kernel(ApplyArgs<T> A, T 
 // batched product: E u for all PDE rows through the cell-bucketed gather
 // (cells.cu), then the warp-per-row combine
 template <typename T, int RPL>
-static int launch_batched(const cpm_ctx *c, const ApplyArgs<T> &A, T m, T n, T rowscale, const T *u, T *a, T *v,
-                          int nrhs, int64_t ld, cudaStream_t st, bool diff) {
-  const int64_t warps = 152 * 64;  // 8 warps per block, 8 blocks per SM
+static int launch_batched(const cpm_ctx *c, const ApplyArgs<T> &A, T m, T n, T rowscale, T cs, const T *u, T *a,
+                          T *v, int nrhs, int64_t ld, cudaStream_t st, bool diff) {
+  // 8 warps per block; by default 8 blocks per SM
+  const int64_t warps = (int64_t)c->nsm * (c->tune.combine_warps_per_sm > 0 ? c->tune.combine_warps_per_sm : 64);
   unsigned g = (unsigned)std::min<int64_t>((A.v.NS + A.v.NC + 7) / 8, warps / 8);
   if (g < 1) g = 1;
-  int launched = 1 + cpm_launch_gather_cells<T>(c, A, u, a, nrhs, ld, st, diff, RPL);
-  if (diff) combine_batched_kernel<T, true, RPL><<<g, 256, 0, st>>>(A, m, n, rowscale, u, a, v, nrhs, ld);
-  else combine_batched_kernel<T, false, RPL><<<g, 256, 0, st>>>(A, m, n, rowscale, u, a, v, nrhs, ld);
+  int launched = 1 + cpm_launch_gather_cells<T>(c, A, cs, u, a, nrhs, ld, st, diff, RPL);
+  if (diff) combine_batched_kernel<T, true, RPL><<<g, 256, 0, st>>>(A, m, n, rowscale, cs, u, a, v, nrhs, ld);
+  else combine_batched_kernel<T, false, RPL><<<g, 256, 0, st>>>(A, m, n, rowscale, cs, u, a, v, nrhs, ld);
   return launched;
 }
 
 __global__ void rhs_kernel(BandView v, const CurveDev *curves, const int32_t *bc_curve, const int32_t *side,
-                           const double *param, const double *s, const double *g, const double *samples, double *f,
-                           int nrhs, int64_t ld) {
+                           const int32_t *type, const double *param, const double *s, const double *g,
+                           const double *samples, double *f, int nrhs, int64_t ld) {
   const int64_t N = v.NS + v.NC;
   CPM_ROWS_COLS_LOOP(N, nrhs, i, r) {
     if (i < v.NS) {
@@ -328,15 +343,16 @@ __global__ void rhs_kernel(BandView v, const CurveDev *curves, const int32_t *bc
         gv = plus;
       }
     }
-    f[i * ld + r] = ((cv.bc == CPM_BC_DIR2) ? 2.0 : 1.0) * gv;
+    f[i * ld + r] = cpm_bc_data_scale(type[al]) * gv;
   }
 }
 
 // dL/dsamples = B^T (c_alpha lambda_alpha): one block per (sample, rhs), a fixed
 // order reduction over the BC DOFs of the sample's curve (deterministic)
 __global__ void boundary_grad_kernel(BandView v, const CurveDev *curves, int ncurves, const int32_t *curve_first,
-                                     const int32_t *side, const double *param, const double *lam, double *out,
-                                     int64_t nsamples_total, int nrhs, int64_t ld) {
+                                     const int32_t *side, const int32_t *type, const double *param,
+                                     const double *lam, double *out, int64_t nsamples_total, int nrhs,
+                                     int64_t ld) {
   __shared__ double red[256];
   for (int64_t q = blockIdx.x; q < nsamples_total * nrhs; q += gridDim.x) {
     int64_t sidx = q / nrhs;
@@ -367,7 +383,7 @@ __global__ void boundary_grad_kernel(BandView v, const CurveDev *curves, int ncu
       double w = 0.0;
       if (i0 == kk) w += 1.0 - fr;
       if (i1 == kk) w += fr;
-      double c = (cv.bc == CPM_BC_DIR2) ? 2.0 : 1.0;
+      const double c = cpm_bc_data_scale(type[al]);
       acc += wblk * w * c * lam[(v.NS + al) * ld + r];
     }
     red[threadIdx.x] = acc;
@@ -408,41 +424,50 @@ ApplyArgs<T> cpm_apply_args(const cpm_ctx *c) {
 }
 
 template <typename T>
-void cpm_launch_gather(const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld, cudaStream_t st, bool diff) {
-  if (diff) gather_kernel<T, true><<<cpm_grid(A.v.NS * nrhs, 256), 256, 0, st>>>(A, u, a, nrhs, ld);
-  else gather_kernel<T, false><<<cpm_grid(A.v.NS * nrhs, 256), 256, 0, st>>>(A, u, a, nrhs, ld);
+void cpm_launch_gather(const ApplyArgs<T> &A, T cs, const T *u, T *a, int nrhs, int64_t ld, cudaStream_t st,
+                       bool diff) {
+  const unsigned g = cpm_grid(A.v.NS * nrhs, 256);
+  if (A.v.np1 == 3) {
+    if (diff) gather_kernel<T, true, 3><<<g, 256, 0, st>>>(A, cs, u, a, nrhs, ld);
+    else gather_kernel<T, false, 3><<<g, 256, 0, st>>>(A, cs, u, a, nrhs, ld);
+  } else {
+    if (diff) gather_kernel<T, true, 4><<<g, 256, 0, st>>>(A, cs, u, a, nrhs, ld);
+    else gather_kernel<T, false, 4><<<g, 256, 0, st>>>(A, cs, u, a, nrhs, ld);
+  }
 }
 
 template <typename T>
-void cpm_launch_combine(const ApplyArgs<T> &A, T m, T n, T rowscale, const T *u, const T *a, T *v, int nrhs,
+void cpm_launch_combine(const ApplyArgs<T> &A, T m, T n, T rowscale, T cs, const T *u, const T *a, T *v, int nrhs,
                         int64_t ld, cudaStream_t st, bool diff) {
   unsigned g = cpm_grid((A.v.NS + A.v.NC) * nrhs, 256);
-  if (diff) combine_kernel<T, true><<<g, 256, 0, st>>>(A, m, n, rowscale, u, a, v, nrhs, ld);
-  else combine_kernel<T, false><<<g, 256, 0, st>>>(A, m, n, rowscale, u, a, v, nrhs, ld);
+  if (diff) combine_kernel<T, true><<<g, 256, 0, st>>>(A, m, n, rowscale, cs, u, a, v, nrhs, ld);
+  else combine_kernel<T, false><<<g, 256, 0, st>>>(A, m, n, rowscale, cs, u, a, v, nrhs, ld);
 }
 
 template ApplyArgs<double> cpm_apply_args<double>(const cpm_ctx *);
 template ApplyArgs<float> cpm_apply_args<float>(const cpm_ctx *);
-template void cpm_launch_gather<double>(const ApplyArgs<double> &, const double *, double *, int, int64_t,
+template void cpm_launch_gather<double>(const ApplyArgs<double> &, double, const double *, double *, int, int64_t,
                                         cudaStream_t, bool);
-template void cpm_launch_gather<float>(const ApplyArgs<float> &, const float *, float *, int, int64_t, cudaStream_t,
-                                       bool);
-template void cpm_launch_combine<double>(const ApplyArgs<double> &, double, double, double, const double *,
+template void cpm_launch_gather<float>(const ApplyArgs<float> &, float, const float *, float *, int, int64_t,
+                                       cudaStream_t, bool);
+template void cpm_launch_combine<double>(const ApplyArgs<double> &, double, double, double, double, const double *,
                                          const double *, double *, int, int64_t, cudaStream_t, bool);
-template void cpm_launch_combine<float>(const ApplyArgs<float> &, float, float, float, const float *, const float *,
-                                        float *, int, int64_t, cudaStream_t, bool);
+template void cpm_launch_combine<float>(const ApplyArgs<float> &, float, float, float, float, const float *,
+                                        const float *, float *, int, int64_t, cudaStream_t, bool);
 
-// v = R A u using the context's scratch for a; R scales the PDE rows by
-// `rowscale` (1 for the plain product) and leaves the BC rows alone
+// v = R A C u using the context's reserved scratch for a (no allocation): R
+// scales the PDE rows of the result by `rowscale` and C the PDE entries of the
+// input by `colscale` (1 and 1 for the plain product); BC rows and BC entries
+// are left alone.  Both forms use the difference form of the gather, which
+// keeps the rounding of smooth fields relative to local differences.
 template <typename T>
-cpm_status cpm_apply_scaled_T(cpm_ctx *c, double m, double n, double rowscale, const T *u, T *v, int nrhs, int64_t ld,
-                              cudaStream_t st) {
-  cpm_status rc = cpm_ensure(c->a_scratch, sizeof(T) * (size_t)c->NS * (size_t)ld);
-  if (rc) return rc;
+cpm_status cpm_apply_rc_T(cpm_ctx *c, double m, double n, double rowscale, double colscale, const T *u, T *v,
+                          int nrhs, int64_t ld, cudaStream_t st) {
+  if (sizeof(T) * (size_t)c->NS * (size_t)ld > c->a_scratch.bytes) return CPM_ERR_CAPACITY;
   ApplyArgs<T> A = cpm_apply_args<T>(c);
   T *a = reinterpret_cast<T *>(c->a_scratch.p);
-  // FP32 uses the difference form (see gather_kernel); FP64 the direct one
-  const bool diff = (sizeof(T) == 4);
+  const bool diff = true;
+  const T cs = T(colscale);
   cpm_prof_begin(c, st);
   // batched layouts whose columns fill whole warps use the warp-per-row kernels
   const bool aligned2 = (ld % 2 == 0) && ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v) |
@@ -450,29 +475,29 @@ cpm_status cpm_apply_scaled_T(cpm_ctx *c, double m, double n, double rowscale, c
   int launched = 2;
   // two adjacent columns per lane need an even column count and 2-element alignment
   if (nrhs > 32 && nrhs <= 64 && nrhs % 2 == 0 && aligned2)
-    launched = launch_batched<T, 2>(c, A, (T)m, (T)n, (T)rowscale, u, a, v, nrhs, ld, st, diff);
+    launched = launch_batched<T, 2>(c, A, (T)m, (T)n, (T)rowscale, cs, u, a, v, nrhs, ld, st, diff);
   else if (nrhs >= 16 && nrhs <= 32)
-    launched = launch_batched<T, 1>(c, A, (T)m, (T)n, (T)rowscale, u, a, v, nrhs, ld, st, diff);
+    launched = launch_batched<T, 1>(c, A, (T)m, (T)n, (T)rowscale, cs, u, a, v, nrhs, ld, st, diff);
   else if (nrhs == 1 && c->ncells > 0) {
-    launched = 1 + cpm_launch_gather1<T>(c, A, u, a, st, diff);
-    cpm_launch_combine<T>(A, (T)m, (T)n, (T)rowscale, u, a, v, nrhs, ld, st, diff);
+    launched = 1 + cpm_launch_gather1<T>(c, A, cs, u, a, st, diff);
+    cpm_launch_combine<T>(A, (T)m, (T)n, (T)rowscale, cs, u, a, v, nrhs, ld, st, diff);
   } else {
-    cpm_launch_gather<T>(A, u, a, nrhs, ld, st, diff);
-    cpm_launch_combine<T>(A, (T)m, (T)n, (T)rowscale, u, a, v, nrhs, ld, st, diff);
+    cpm_launch_gather<T>(A, cs, u, a, nrhs, ld, st, diff);
+    cpm_launch_combine<T>(A, (T)m, (T)n, (T)rowscale, cs, u, a, v, nrhs, ld, st, diff);
   }
   cpm_prof_end(c, st, c->NS * (int64_t)nrhs);
   cpm_count_launches(c, launched);
   CPM_CUDA_TRY(cudaGetLastError());
   return CPM_OK;
 }
-template cpm_status cpm_apply_scaled_T<double>(cpm_ctx *, double, double, double, const double *, double *, int,
-                                               int64_t, cudaStream_t);
-template cpm_status cpm_apply_scaled_T<float>(cpm_ctx *, double, double, double, const float *, float *, int, int64_t,
-                                              cudaStream_t);
+template cpm_status cpm_apply_rc_T<double>(cpm_ctx *, double, double, double, double, const double *, double *, int,
+                                           int64_t, cudaStream_t);
+template cpm_status cpm_apply_rc_T<float>(cpm_ctx *, double, double, double, double, const float *, float *, int,
+                                          int64_t, cudaStream_t);
 
 template <typename T>
 cpm_status cpm_apply_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld, cudaStream_t st) {
-  return cpm_apply_scaled_T<T>(c, m, n, 1.0, u, v, nrhs, ld, st);
+  return cpm_apply_rc_T<T>(c, m, n, 1.0, 1.0, u, v, nrhs, ld, st);
 }
 template cpm_status cpm_apply_T<double>(cpm_ctx *, double, double, const double *, double *, int, int64_t,
                                         cudaStream_t);
@@ -503,7 +528,7 @@ void cpm_prof_end(cpm_ctx *c, cudaStream_t st, int64_t row_rhs) {
 
 cpm_status cpm_internal_extend(cpm_ctx *c, const double *u, double *a, int nrhs, int64_t ld, cudaStream_t st) {
   ApplyArgs<double> A = cpm_apply_args<double>(c);
-  cpm_launch_gather<double>(A, u, a, nrhs, ld, st, false);
+  cpm_launch_gather<double>(A, 1.0, u, a, nrhs, ld, st, false);
   CPM_CUDA_TRY(cudaGetLastError());
   return CPM_OK;
 }
@@ -511,7 +536,8 @@ cpm_status cpm_internal_extend(cpm_ctx *c, const double *u, double *a, int nrhs,
 cpm_status cpm_internal_rhs(cpm_ctx *c, const double *s, const double *g, const double *samples, double *f, int nrhs,
                             int64_t ld, cudaStream_t st) {
   int64_t N = c->NS + c->NC;
-  rhs_kernel<<<cpm_grid(N * nrhs, 256), 256, 0, st>>>(c->view(), c->d_curves, c->d_bc_curve, c->d_side, c->d_param, s,
+  rhs_kernel<<<cpm_grid(N * nrhs, 256), 256, 0, st>>>(c->view(), c->d_curves, c->d_bc_curve, c->d_side, c->d_bc_type,
+                                                      c->d_param, s,
                                                       g, samples, f, nrhs, ld);
   CPM_CUDA_TRY(cudaGetLastError());
   return CPM_OK;
@@ -520,26 +546,13 @@ cpm_status cpm_internal_rhs(cpm_ctx *c, const double *s, const double *g, const 
 cpm_status cpm_internal_boundary_grad(cpm_ctx *c, const double *lam, double *out, int nrhs, int64_t ld,
                                       cudaStream_t st) {
   if (c->nsamples_total == 0) return CPM_OK;
-  // first BC DOF of each curve (BC DOFs are ordered by curve)
-  int n = c->ncurves;
-  std::vector<int32_t> first(n + 1, 0);
-  {
-    std::vector<int32_t> bcc(c->NC);
-    if (c->NC) CPM_CUDA_TRY(cudaMemcpyAsync(bcc.data(), c->d_bc_curve, sizeof(int32_t) * c->NC, cudaMemcpyDeviceToHost, st));
-    CPM_CUDA_TRY(cudaStreamSynchronize(st));
-    for (int k = 0; k <= n; ++k) first[k] = 0;
-    for (int64_t a = 0; a < c->NC; ++a) first[bcc[a] + 1]++;
-    for (int k = 0; k < n; ++k) first[k + 1] += first[k];
-  }
-  int32_t *d_first = nullptr;
-  CPM_CUDA_TRY(cudaMallocAsync(&d_first, sizeof(int32_t) * (n + 1), st));
-  CPM_CUDA_TRY(cudaMemcpyAsync(d_first, first.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st));
-  unsigned grid = (unsigned)std::min<int64_t>(c->nsamples_total * nrhs, 152 * 32);
-  boundary_grad_kernel<<<grid, 256, 0, st>>>(c->view(), c->d_curves, n, d_first, c->d_side, c->d_param, lam, out,
-                                             c->nsamples_total, nrhs, ld);
+  // c->d_curve_first: first BC DOF of each curve (BC DOFs are ordered by curve),
+  // built with the boundary
+  unsigned grid = (unsigned)std::min<int64_t>(c->nsamples_total * nrhs, (int64_t)c->nsm * 32);
+  boundary_grad_kernel<<<grid, 256, 0, st>>>(c->view(), c->d_curves, c->ncurves, c->d_curve_first, c->d_side,
+                                             c->d_bc_type, c->d_param, lam, out, c->nsamples_total, nrhs, ld);
+  cpm_count_launches(c, 1);
   CPM_CUDA_TRY(cudaGetLastError());
-  CPM_CUDA_TRY(cudaFreeAsync(d_first, st));
-  CPM_CUDA_TRY(cudaStreamSynchronize(st));
   return CPM_OK;
 }
 
@@ -585,17 +598,17 @@ cpm_status cpm_apply_noalloc_T(cpm_ctx *c, double m, double n, const T *u, T *v,
   if (rc) return rc;
   T *a = reinterpret_cast<T *>(p);
   ApplyArgs<T> A = cpm_apply_args<T>(c);
-  const bool diff = (sizeof(T) == 4);
+  const bool diff = true;  // the same arithmetic as cpm_apply
   const bool aligned2 = (ld % 2 == 0) && ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v) |
                                            reinterpret_cast<uintptr_t>(a)) % (2 * sizeof(T)) == 0);
   int launched = 2;
   if (nrhs > 32 && nrhs <= 64 && nrhs % 2 == 0 && aligned2)
-    launched = launch_batched<T, 2>(c, A, (T)m, (T)n, T(1), u, a, v, nrhs, ld, st, diff);
+    launched = launch_batched<T, 2>(c, A, (T)m, (T)n, T(1), T(1), u, a, v, nrhs, ld, st, diff);
   else if (nrhs >= 16 && nrhs <= 32)
-    launched = launch_batched<T, 1>(c, A, (T)m, (T)n, T(1), u, a, v, nrhs, ld, st, diff);
+    launched = launch_batched<T, 1>(c, A, (T)m, (T)n, T(1), T(1), u, a, v, nrhs, ld, st, diff);
   else {
-    cpm_launch_gather<T>(A, u, a, nrhs, ld, st, diff);
-    cpm_launch_combine<T>(A, (T)m, (T)n, T(1), u, a, v, nrhs, ld, st, diff);
+    cpm_launch_gather<T>(A, T(1), u, a, nrhs, ld, st, diff);
+    cpm_launch_combine<T>(A, (T)m, (T)n, T(1), T(1), u, a, v, nrhs, ld, st, diff);
   }
   cpm_count_launches(c, launched);
   CPM_CUDA_TRY(cudaGetLastError());

@@ -25,16 +25,19 @@ struct ApplyArgs {
 template <typename T>
 ApplyArgs<T> cpm_apply_args(const cpm_ctx *c);
 template <typename T>
-void cpm_launch_gather(const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld, cudaStream_t st, bool diff);
+void cpm_launch_gather(const ApplyArgs<T> &A, T cs, const T *u, T *a, int nrhs, int64_t ld, cudaStream_t st,
+                       bool diff);
 template <typename T>
-void cpm_launch_combine(const ApplyArgs<T> &A, T m, T n, T rowscale, const T *u, const T *a, T *v, int nrhs,
+void cpm_launch_combine(const ApplyArgs<T> &A, T m, T n, T rowscale, T cs, const T *u, const T *a, T *v, int nrhs,
                         int64_t ld, cudaStream_t st, bool diff);
+// v = R A C u: R scales the PDE rows of the result, C the PDE entries of the
+// input (diagonal row scaling and right preconditioning without extra vectors)
 template <typename T>
-cpm_status cpm_apply_scaled_T(cpm_ctx *c, double m, double n, double rowscale, const T *u, T *v, int nrhs, int64_t ld,
-                              cudaStream_t st);
+cpm_status cpm_apply_rc_T(cpm_ctx *c, double m, double n, double rowscale, double colscale, const T *u, T *v,
+                          int nrhs, int64_t ld, cudaStream_t st);
 template <typename T>
-cpm_status cpm_apply_transpose_scaled_T(cpm_ctx *c, double m, double n, double rowscale, const T *u, T *v, int nrhs,
-                                        int64_t ld, cudaStream_t st);
+cpm_status cpm_apply_transpose_rc_T(cpm_ctx *c, double m, double n, double rowscale, double colscale, const T *u,
+                                    T *v, int nrhs, int64_t ld, cudaStream_t st);
 // the product with the intermediate in a fixed module array (no allocation)
 template <typename T>
 cpm_status cpm_apply_noalloc_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld,
@@ -49,7 +52,7 @@ cpm_status cpm_apply_transpose_T(cpm_ctx *c, double m, double n, const T *u, T *
 // cell-bucketed E u for all PDE rows plus the flipped-entry correction of the
 // rows near curves (batched layouts); returns the number of kernels launched
 template <typename T>
-int cpm_launch_gather_cells(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u, T *a, int nrhs, int64_t ld,
+int cpm_launch_gather_cells(const cpm_ctx *c, const ApplyArgs<T> &A, T cs, const T *u, T *a, int nrhs, int64_t ld,
                             cudaStream_t st, bool diff, int rpl);
 
 cpm_status cpm_internal_surface_gradient(cpm_ctx *c, const double *u, double *X, int normalize, cudaStream_t st);
@@ -57,13 +60,20 @@ cpm_status cpm_internal_surface_divergence(cpm_ctx *c, const double *X, double *
 // single right-hand side: E u for all PDE rows in cell order plus the
 // flipped-entry correction; returns the number of kernels launched
 template <typename T>
-int cpm_launch_gather1(const cpm_ctx *c, const ApplyArgs<T> &A, const T *u, T *a, cudaStream_t st, bool diff);
+int cpm_launch_gather1(const cpm_ctx *c, const ApplyArgs<T> &A, T cs, const T *u, T *a, cudaStream_t st, bool diff);
+
+// the cell gather's default x passes for a stencil of np1 nodes per axis, the
+// precision and the columns per lane (1 or 2); the autotuner starts from it
+int cpm_cells_default_xh(int np1, bool fp64, int rpl);
 
 cpm_status cpm_internal_extend(cpm_ctx *c, const double *u, double *a, int nrhs, int64_t ld, cudaStream_t st);
 cpm_status cpm_internal_rhs(cpm_ctx *c, const double *s, const double *g, const double *samples, double *f, int nrhs,
                             int64_t ld, cudaStream_t st);
 cpm_status cpm_internal_boundary_grad(cpm_ctx *c, const double *lam, double *out, int nrhs, int64_t ld,
                                       cudaStream_t st);
-cpm_status cpm_internal_band_build(cpm_ctx *c, const cpm_shape_desc *s, double h, double r_band);
+cpm_status cpm_internal_band_build(cpm_ctx *c, const cpm_shape_desc *s, double h, int p, double r_band);
 void cpm_internal_free_band(cpm_ctx *c);
 cpm_status cpm_internal_set_boundary(cpm_ctx *c, const cpm_curve_desc *curves, int n);
+cpm_status cpm_internal_autotune(cpm_ctx *c, int nrhs, int64_t ld, int prec, cpm_tune_info *info, cudaStream_t st);
+cpm_status cpm_internal_set_tune(cpm_ctx *c, int nrhs, int prec, const cpm_tune_info *info);
+

@@ -15,6 +15,7 @@
 // (every workload here) the two sets coincide.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -55,8 +56,17 @@ __global__ void __launch_bounds__(512) eval_bricks_kernel(ShapeDev shape, int di
         // Newton iteration (App. A) can fail to converge only far from the
         // surface (deep inside, near the bumps' medial axes), at nodes that
         // bricks reach but the band does not: they are taken as outside, and
-        // every stencil node of every band row is checked present afterwards
-        if (shape.kind != CPM_SHAPE_BUMPY) atomicOr(err, CPM_DEVERR_CP);
+        // every stencil node of every band row is checked present afterwards.
+        // A failure where the first-order distance estimate |phi| / |grad phi|
+        // puts the node inside the band is a genuine failure near S.
+        if (shape.kind != CPM_SHAPE_BUMPY) {
+          atomicOr(err, CPM_DEVERR_CP);
+        } else {
+          double phi, g[3];
+          cpm_bumpy::bumpy_eval(shape, x, &phi, g, nullptr);
+          const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+          if (!(gn > 0.0) || fabs(phi) <= rband * gn) atomicOr(err, CPM_DEVERR_CP);
+        }
       } else {
         double d[3] = {rn_sub(x[0], cp[0]), rn_sub(x[1], cp[1]), rn_sub(x[2], cp[2])};
         member = rn_norm3(d) <= rband;
@@ -177,7 +187,7 @@ __global__ void row_stencil_kernel(BandView v, const double *cp, const unsigned 
     double y[3] = {cp[i * 3], cp[i * 3 + 1], cp[i * 3 + 2]};
     int base[3];
     double t[3];
-    cpm_stencil_of(v.dim, v.h, y, base, t);
+    cpm_stencil_of(v.dim, v.h, v.np1, y, base, t);
     int bb[3] = {base[0] >> 3, base[1] >> 3, base[2] >> 3};
     int64_t p = cpm_hash_find(hkeys, hcap, (uint64_t)cpm_brick_key(bb[0], bb[1], bb[2]));
     int32_t b = (p < 0) ? -1 : slot_to_sorted[p];
@@ -187,10 +197,10 @@ __global__ void row_stencil_kernel(BandView v, const double *cp, const unsigned 
     } else {
       int lx = base[0] & 7, ly = base[1] & 7, lz = base[2] & 7;
       rbase[i] = ((uint32_t)b << 9) | (uint32_t)(lz * 64 + ly * 8 + lx);
-      int nz = (v.dim == 3) ? 4 : 1;
+      const int np1 = v.np1, nz = (v.dim == 3) ? np1 : 1;
       for (int cz = 0; cz < nz; ++cz)
-        for (int cy = 0; cy < 4; ++cy)
-          for (int cx = 0; cx < 4; ++cx)
+        for (int cy = 0; cy < np1; ++cy)
+          for (int cx = 0; cx < np1; ++cx)
             if (cpm_node_index(v, b, lx + cx, ly + cy, lz + cz) < 0) atomicOr(err, CPM_DEVERR_MISSING_NODE);
     }
     for (int a = 0; a < 3; ++a) {
@@ -217,6 +227,21 @@ cpm_status cpm_internal_cuda_err(cudaError_t e) {
   return (e == cudaErrorMemoryAllocation) ? CPM_ERR_OOM : CPM_ERR_CUDA;
 }
 
+int cpm_device_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { (void)cudaGetLastError(); return 152; }
+  if (cached[dev] <= 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      (void)cudaGetLastError();
+      n = 152;
+    }
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
 cpm_status cpm_ensure(WorkBuf &b, size_t bytes) {
   if (b.bytes >= bytes) return CPM_OK;
   if (b.p) cudaFree(b.p);
@@ -227,8 +252,9 @@ cpm_status cpm_ensure(WorkBuf &b, size_t bytes) {
   return CPM_OK;
 }
 
-static double eq3_radius(int dim, double h) {
-  double half = (3.0 + 1.0) / 2.0;
+// Eq. (3) with q = 1
+static double eq3_radius(int dim, int p, double h) {
+  double half = ((double)p + 1.0) / 2.0;
   return h * std::sqrt((double)(dim - 1) * (half * half) + (1.0 + half) * (1.0 + half));
 }
 
@@ -270,7 +296,7 @@ static cpm_status build_once(cpm_ctx *c, int64_t hcap) {
     while (nfront > 0) {
       if (++iters > max_iters) { rc = CPM_ERR_TIMEOUT; goto done; }
       TRY(cudaMemsetAsync(d_next_n, 0, sizeof(int), st));
-      int grid = std::min(nfront, 152 * 8);
+      int grid = std::min(nfront, c->nsm * 8);
       eval_bricks_kernel<<<grid, 512, 0, st>>>(c->shape, c->dim, c->h, c->rband, hkeys, hcap, hmask, front, nfront,
                                                next, d_next_n, n_ins, c->d_err);
       TRY(cudaGetLastError());
@@ -321,7 +347,7 @@ static cpm_status build_once(cpm_ctx *c, int64_t hcap) {
   TRY(cudaMalloc(&c->d_rbase, sizeof(uint32_t) * c->NS));
   TRY(cudaMalloc(&c->d_t64, sizeof(double) * c->NS * 3));
   TRY(cudaMalloc(&c->d_t32, sizeof(float) * c->NS * 3));
-  nodes_kernel<<<(unsigned)std::min<int64_t>(c->nb, 152 * 16), 512, 0, st>>>(
+  nodes_kernel<<<(unsigned)std::min<int64_t>(c->nb, (int64_t)c->nsm * 16), 512, 0, st>>>(
       c->shape, c->dim, c->h, c->d_bkey, c->d_bmask, c->d_brank, c->d_bstart, c->nb, c->d_ijk, c->d_cp, c->d_rself,
       c->d_err);
   v = c->view();
@@ -360,13 +386,20 @@ static void free_band(cpm_ctx *c) {
   c->nb = 0; c->NS = 0;
 }
 
-cpm_status cpm_internal_band_build(cpm_ctx *c, const cpm_shape_desc *s, double h, double r_band) {
+cpm_status cpm_internal_band_build(cpm_ctx *c, const cpm_shape_desc *s, double h, int p, double r_band) {
   c->dim = s->dim;
   c->h = h;
-  c->rband = (r_band > 0) ? r_band : eq3_radius(s->dim, h);
+  c->p = p;
+  c->rband = (r_band > 0) ? r_band : eq3_radius(s->dim, p, h);
   for (int a = 0; a < 3; ++a) c->shape_seed[a] = s->seed[a];
   c->shape.kind = s->kind; c->shape.dim = s->dim; c->shape.K = s->K;
   c->shape.R = s->R; c->shape.rt = s->rt; c->shape.amp = s->amp; c->shape.width = s->width;
+  c->shape.newton_maxit = 200;
+  // test hook: a forced small iteration cap makes the projection fail next to S
+  if (const char *e = std::getenv("CPM_NEWTON_MAXIT")) {
+    const int v = std::atoi(e);
+    if (v >= 1) c->shape.newton_maxit = v;
+  }
   if (s->K > 0) {
     CPM_CUDA_TRY(cudaMalloc(&c->d_shape_a, sizeof(double) * s->K));
     CPM_CUDA_TRY(cudaMalloc(&c->d_shape_c, sizeof(double) * 3 * s->K));
@@ -380,6 +413,14 @@ cpm_status cpm_internal_band_build(cpm_ctx *c, const cpm_shape_desc *s, double h
   double bricks = nodes / (s->dim == 3 ? 512.0 : 64.0) * 6.0 + 1024.0;
   int64_t hcap = 1 << 12;
   while ((double)hcap < 4.0 * bricks) hcap <<= 1;
+  // test hook: a forced small initial capacity exercises the overflow retry
+  if (const char *e = std::getenv("CPM_HASH_CAP_INIT")) {
+    const long long v = std::atoll(e);
+    if (v >= 16) {
+      hcap = 16;
+      while (hcap < v) hcap <<= 1;
+    }
+  }
   cpm_status rc = CPM_ERR_CAPACITY;
   for (int attempt = 0; attempt < 4 && rc == CPM_ERR_CAPACITY; ++attempt) {
     free_band(c);

@@ -11,10 +11,14 @@
 //  * On-C tie (Sec. 4.2): |cp_{S-C}(x)| < 0.1 h^2 means cp_S(x) lies on C and may
 //    take either side; the node takes the side of the first node of its own
 //    interpolation stencil (x fastest, then y, then z) whose vector is longer.
-//  * Dirichlet BC rows (Sec. 4.3): first order u_alpha = g; second order
-//    u_alpha + sum_beta wbar_beta u_sigma(beta) = 2 g with the stencil at
-//    cpbar_C(x) = cp_S(2 cp_C(x) - x), where the default column is the BC twin,
-//    replaced by the PDE DOF when d*_alpha . cp_{S-C}(x_beta) < 0 (Eq. 11).
+//  * BC rows (Sec. 4.3), with the type of the side the BC DOF stands in for
+//    (the side opposite cp_S(x_alpha); mixed types per side, Sec. 4.2):
+//      DIR1 u_alpha = g;  DIR2 u_alpha + sum_beta wbar_beta u_sigma(beta) = 2 g;
+//      NEU1 u_alpha - sum_beta w_beta u_sigma(beta) = 0 with the stencil at
+//      cp_C(x_alpha);  NEU2 as NEU1 with the stencil at the mirror point
+//      cpbar_C(x) = cp_S(2 cp_C(x) - x), which DIR2 uses too.  A stencil's
+//      default column is the BC twin, replaced by the PDE DOF when
+//      d*_alpha . cp_{S-C}(x_beta) < 0 (Eq. 11).
 //
 // Geometry uses explicit round-to-nearest FP64 operations so that every flip
 // decision is reproducible bit for bit.
@@ -70,11 +74,11 @@ __device__ void zhat(const BView &b, const CurveDev &cv, int32_t j, double z[3])
   double y[3] = {b.cp[3 * j], b.cp[3 * j + 1], b.cp[3 * j + 2]};
   int base[3];
   double t[3];
-  cpm_stencil_of(b.v.dim, b.v.h, y, base, t);
-  int nz = (b.v.dim == 3) ? 4 : 1;
+  cpm_stencil_of(b.v.dim, b.v.h, b.v.np1, y, base, t);
+  const int np1 = b.v.np1, nz = (b.v.dim == 3) ? np1 : 1;
   for (int cz = 0; cz < nz; ++cz)
-    for (int cy = 0; cy < 4; ++cy)
-      for (int cx = 0; cx < 4; ++cx) {
+    for (int cy = 0; cy < np1; ++cy)
+      for (int cx = 0; cx < np1; ++cx) {
         int32_t q = lookup_near(b, j, base[0] + cx, base[1] + cy, (b.v.dim == 3) ? base[2] + cz : 0);
         if (q < 0) continue;
         double w[3];
@@ -142,9 +146,10 @@ __global__ void assign_spec_kernel(const int8_t *near, const int32_t *pos, int64
   }
 }
 
-// per BC DOF: cp_C, side of cp_S (sign of zhat . nu; none for a point in 3D), angle
+// per BC DOF: cp_C, side of cp_S (sign of zhat . nu; none for a point in 3D),
+// angle, and the row's BC type (that of the opposite side)
 __global__ void bc_info_kernel(BView b, const int32_t *twin, const int32_t *bc_curve, int64_t NC, double *cpc,
-                               int32_t *side, double *param) {
+                               int32_t *side, double *param, int32_t *type) {
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < NC; a += (int64_t)gridDim.x * blockDim.x) {
     int32_t j = twin[a];
     const CurveDev &cv = b.curves[bc_curve[a]];
@@ -155,6 +160,7 @@ __global__ void bc_info_kernel(BView b, const int32_t *twin, const int32_t *bc_c
     zhat(b, cv, j, z);
     double s = rn_dot3(z, cv.nu);
     side[a] = (cv.kind == CPM_CURVE_POINT && b.v.dim == 3) ? 0 : ((s > 0.0) - (s < 0.0));
+    type[a] = (side[a] > 0) ? cv.bc_minus : cv.bc;
     double ang = 0.0;
     if (cv.kind == CPM_CURVE_CIRCLE) {
       double q[3] = {cc[0] - cv.p[0], cc[1] - cv.p[1], cc[2] - cv.p[2]};
@@ -197,14 +203,19 @@ __global__ void spec_stencil_kernel(BView b, const int32_t *spec_row, int64_t ns
     double y[3] = {b.cp[3 * i], b.cp[3 * i + 1], b.cp[3 * i + 2]};
     int base[3];
     double t[3], w[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {1, 0, 0, 0}};
-    cpm_stencil_of(b.v.dim, b.v.h, y, base, t);
-    for (int a = 0; a < b.v.dim; ++a) cpm_lagrange4<double>(t[a], w[a]);
-    int nz = (b.v.dim == 3) ? 4 : 1;
+    const int np1 = b.v.np1;
+    cpm_stencil_of(b.v.dim, b.v.h, np1, y, base, t);
+    for (int a = 0; a < b.v.dim; ++a) cpm_lagrange_rt<double>(np1, t[a], w[a]);
+    // explicit stencil in the fixed 4 x 4 x 4 layout; entries outside the
+    // np1^dim stencil are absent (-1)
     int e = 0;
     for (int cz = 0; cz < 4; ++cz)
       for (int cy = 0; cy < 4; ++cy)
         for (int cx = 0; cx < 4; ++cx, ++e) {
-          if (cz >= nz) { ecol[s * 64 + e] = -1; ew[s * 64 + e] = 0.0; ew32[s * 64 + e] = 0.0f; continue; }
+          if (!cpm_in_stencil(e, np1, b.v.dim)) {
+            ecol[s * 64 + e] = -1; ew[s * 64 + e] = 0.0; ew32[s * 64 + e] = 0.0f;
+            continue;
+          }
           int32_t j = lookup_near(b, i, base[0] + cx, base[1] + cy, (b.v.dim == 3) ? base[2] + cz : 0);
           if (j < 0) { atomicOr(err, CPM_DEVERR_MISSING_NODE); j = i; }
           double wt = w[0][cx] * w[1][cy] * w[2][cz];
@@ -225,10 +236,10 @@ __global__ void spec_stencil_kernel(BView b, const int32_t *spec_row, int64_t ns
   }
 }
 
-// Dirichlet BC rows
-__global__ void bc_rows_kernel(BView b, const int32_t *twin, const int32_t *bc_curve, const double *cpc, int64_t NC,
-                               const int32_t *bc_of, int32_t *cnt, int32_t *col, double *val, float *val32,
-                               unsigned *err) {
+// BC rows
+__global__ void bc_rows_kernel(BView b, const int32_t *twin, const int32_t *bc_curve, const int32_t *type,
+                               const double *cpc, int64_t NC, const int32_t *bc_of, int32_t *cnt, int32_t *col,
+                               double *val, float *val32, unsigned *err) {
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < NC; a += (int64_t)gridDim.x * blockDim.x) {
     int32_t j = twin[a];
     int k = bc_curve[a];
@@ -237,20 +248,28 @@ __global__ void bc_rows_kernel(BView b, const int32_t *twin, const int32_t *bc_c
     col[o] = (int32_t)(b.v.NS + a);
     val[o] = 1.0;
     val32[o] = 1.0f;
-    if (cv.bc != CPM_BC_DIR2) { cnt[a] = 1; continue; }
+    const int ty = type[a];
+    if (ty == CPM_BC_DIR1) { cnt[a] = 1; continue; }
     double dstar[3], x[3], yv[3], cpb[3];
     zhat(b, cv, j, dstar);
-    node_coords(b, j, x);
-    for (int e = 0; e < 3; ++e) yv[e] = rn_sub(rn_mul(2.0, cpc[3 * a + e]), x[e]);
-    if (cpm_cp_S(b.shape, yv, cpb)) { atomicOr(err, CPM_DEVERR_CP); cnt[a] = 1; continue; }
+    if (ty == CPM_BC_NEU1) {
+      // first-order Neumann: the query point is cp_C(x_alpha) itself
+      for (int e = 0; e < 3; ++e) cpb[e] = cpc[3 * a + e];
+    } else {
+      node_coords(b, j, x);
+      for (int e = 0; e < 3; ++e) yv[e] = rn_sub(rn_mul(2.0, cpc[3 * a + e]), x[e]);
+      if (cpm_cp_S(b.shape, yv, cpb)) { atomicOr(err, CPM_DEVERR_CP); cnt[a] = 1; continue; }
+    }
+    const double sgn = (ty == CPM_BC_DIR2) ? 1.0 : -1.0;
     int base[3];
     double t[3], w[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {1, 0, 0, 0}};
-    cpm_stencil_of(b.v.dim, b.v.h, cpb, base, t);
-    for (int e = 0; e < b.v.dim; ++e) cpm_lagrange4<double>(t[e], w[e]);
-    int nz = (b.v.dim == 3) ? 4 : 1, n = 1;
+    const int np1 = b.v.np1;
+    cpm_stencil_of(b.v.dim, b.v.h, np1, cpb, base, t);
+    for (int e = 0; e < b.v.dim; ++e) cpm_lagrange_rt<double>(np1, t[e], w[e]);
+    int nz = (b.v.dim == 3) ? np1 : 1, n = 1;
     for (int cz = 0; cz < nz; ++cz)
-      for (int cy = 0; cy < 4; ++cy)
-        for (int cx = 0; cx < 4; ++cx) {
+      for (int cy = 0; cy < np1; ++cy)
+        for (int cx = 0; cx < np1; ++cx) {
           int32_t q = lookup_near(b, j, base[0] + cx, base[1] + cy, (b.v.dim == 3) ? base[2] + cz : 0);
           if (q < 0) { atomicOr(err, CPM_DEVERR_MISSING_NODE); continue; }
           double z[3];
@@ -260,7 +279,7 @@ __global__ void bc_rows_kernel(BView b, const int32_t *twin, const int32_t *bc_c
             int32_t t2 = bc_of[q];
             if (t2 >= 0 && bc_curve[t2 - b.v.NS] == k) c = t2;
           }
-          double wt = w[0][cx] * w[1][cy] * w[2][cz];
+          double wt = sgn * (w[0][cx] * w[1][cy] * w[2][cz]);
           col[o + n] = c;
           val[o + n] = wt;
           val32[o + n] = (float)wt;
@@ -275,7 +294,11 @@ __global__ void bc_rows_kernel(BView b, const int32_t *twin, const int32_t *bc_c
 void cpm_free_boundary(cpm_ctx *c) {
   cudaFree(c->d_curves); cudaFree(c->d_bc_of); cudaFree(c->d_near); cudaFree(c->d_twin); cudaFree(c->d_bc_curve);
   cudaFree(c->d_cpc); cudaFree(c->d_side); cudaFree(c->d_param); cudaFree(c->d_bc_cnt); cudaFree(c->d_bc_col);
+  cudaFree(c->d_bc_type);
+  c->d_bc_type = nullptr;
   cudaFree(c->d_bc_val); cudaFree(c->d_bc_val32); cudaFree(c->d_spec_row); cudaFree(c->d_spec_of);
+  cudaFree(c->d_curve_first);
+  c->d_curve_first = nullptr;
   cudaFree(c->d_spec_ecol); cudaFree(c->d_spec_ew); cudaFree(c->d_spec_ew32); cudaFree(c->d_spec_fcol);
   cpm_free_cells(c);
   cudaFree(c->d_T_ptr); cudaFree(c->d_T_row); cudaFree(c->d_cellid); cudaFree(c->d_w1d64); cudaFree(c->d_w1d32);
@@ -303,6 +326,7 @@ cpm_status cpm_internal_set_boundary(cpm_ctx *c, const cpm_curve_desc *curves, i
     CurveDev &d = c->h_curves[k];
     const cpm_curve_desc &s = curves[k];
     d.kind = s.kind; d.bc = s.bc; d.two_sided = s.two_sided; d.n_samples = s.n_samples;
+    d.bc_minus = s.bc_minus ? s.bc_minus : s.bc;
     for (int e = 0; e < 3; ++e) { d.p[e] = s.p[e]; d.nu[e] = s.nu[e]; d.ref[e] = s.ref[e]; }
     d.rad = s.rad;
     d.sample_off = off;
@@ -352,11 +376,20 @@ cpm_status cpm_internal_set_boundary(cpm_ctx *c, const cpm_curve_desc *curves, i
   for (int k = 0; k < n; ++k) c->NC += counts[k];
   b.v.NC = c->NC;
   {
+    // first BC DOF of each curve (BC DOFs are numbered curve by curve)
+    std::vector<int32_t> first(n + 1, 0);
+    for (int k = 0; k < n; ++k) first[k + 1] = first[k] + counts[k];
+    TRY(cudaMalloc(&c->d_curve_first, sizeof(int32_t) * (n + 1)));
+    TRY(cudaMemcpyAsync(c->d_curve_first, first.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st));
+    TRY(cudaStreamSynchronize(st));
+  }
+  {
     int64_t nc1 = c->NC > 0 ? c->NC : 1;
     TRY(cudaMalloc(&c->d_twin, sizeof(int32_t) * nc1));
     TRY(cudaMalloc(&c->d_bc_curve, sizeof(int32_t) * nc1));
     TRY(cudaMalloc(&c->d_cpc, sizeof(double) * 3 * nc1));
     TRY(cudaMalloc(&c->d_side, sizeof(int32_t) * nc1));
+    TRY(cudaMalloc(&c->d_bc_type, sizeof(int32_t) * nc1));
     TRY(cudaMalloc(&c->d_param, sizeof(double) * nc1));
     TRY(cudaMalloc(&c->d_bc_cnt, sizeof(int32_t) * nc1));
     TRY(cudaMalloc(&c->d_bc_col, sizeof(int32_t) * CPM_BC_STRIDE * nc1));
@@ -386,14 +419,15 @@ cpm_status cpm_internal_set_boundary(cpm_ctx *c, const cpm_curve_desc *curves, i
                                                              c->d_rbase);
     if (c->NC > 0)
       bc_info_kernel<<<cpm_grid(c->NC, 128), 128, 0, st>>>(b, c->d_twin, c->d_bc_curve, c->NC, c->d_cpc, c->d_side,
-                                                           c->d_param);
+                                                           c->d_param, c->d_bc_type);
     if (c->nspec > 0)
       spec_stencil_kernel<<<cpm_grid(c->nspec, 64), 64, 0, st>>>(b, c->d_spec_row, c->nspec, c->d_near, c->d_bc_of,
                                                                  c->d_bc_curve, c->d_spec_ecol, c->d_spec_ew,
                                                                  c->d_spec_ew32, c->d_spec_fcol, c->d_counter,
                                                                  c->d_err);
     if (c->NC > 0)
-      bc_rows_kernel<<<cpm_grid(c->NC, 64), 64, 0, st>>>(b, c->d_twin, c->d_bc_curve, c->d_cpc, c->NC, c->d_bc_of,
+      bc_rows_kernel<<<cpm_grid(c->NC, 64), 64, 0, st>>>(b, c->d_twin, c->d_bc_curve, c->d_bc_type, c->d_cpc, c->NC,
+                                                         c->d_bc_of,
                                                          c->d_bc_cnt, c->d_bc_col, c->d_bc_val, c->d_bc_val32,
                                                          c->d_err);
     TRY(cudaGetLastError());

@@ -6,7 +6,8 @@
 //   grad phi = u - q/s,   D^2 phi = P/s - [P H P - u q^T - q u^T - (u.g) P]/s^2.
 // Stage 1: cp <- cp - phi grad/|grad|^2 until the step is below 1e-10.
 // Stage 2: Newton on f(cp, lam) = |cp - x|^2/2 + lam phi(cp), lam_0 from stage 1,
-// until |dy| < 1e-10.  Both stages stop after 200 iterations with failure.
+// until |dy| < 1e-10.  Both stages stop after s.newton_maxit (200) iterations
+// with failure.
 #pragma once
 
 namespace cpm_bumpy {
@@ -75,18 +76,19 @@ __device__ inline int cpm_cp_bumpy(const ShapeDev &s, const double *x, double *c
   using namespace cpm_bumpy;
   double y[3] = {x[0], x[1], x[2]}, phi, gr[3], H[9];
   int it;
-  for (it = 0; it < 200; ++it) {
+  const int maxit = s.newton_maxit;
+  for (it = 0; it < maxit; ++it) {
     bumpy_eval(s, y, &phi, gr, nullptr);
     double g2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
     double st[3] = {phi * gr[0] / g2, phi * gr[1] / g2, phi * gr[2] / g2};
     y[0] -= st[0]; y[1] -= st[1]; y[2] -= st[2];
     if (sqrt(st[0] * st[0] + st[1] * st[1] + st[2] * st[2]) < 1e-10) break;
   }
-  if (it == 200) return 1;
+  if (it == maxit) return 1;
   bumpy_eval(s, y, &phi, gr, nullptr);
   double lam = ((x[0] - y[0]) * gr[0] + (x[1] - y[1]) * gr[1] + (x[2] - y[2]) * gr[2]) /
                (gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-  for (it = 0; it < 200; ++it) {
+  for (it = 0; it < maxit; ++it) {
     bumpy_eval(s, y, &phi, gr, H);
     double J[16], F[4], dy[4];
     for (int i = 0; i < 3; ++i) {
@@ -102,7 +104,7 @@ __device__ inline int cpm_cp_bumpy(const ShapeDev &s, const double *x, double *c
     lam -= dy[3];
     if (sqrt(dy[0] * dy[0] + dy[1] * dy[1] + dy[2] * dy[2] + dy[3] * dy[3]) < 1e-10) break;
   }
-  if (it == 200) return 1;
+  if (it == maxit) return 1;
   cp[0] = y[0]; cp[1] = y[1]; cp[2] = y[2];
   return 0;
 }

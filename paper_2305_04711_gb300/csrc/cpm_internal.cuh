@@ -36,12 +36,14 @@
 
 struct CurveDev {
   int kind, bc, two_sided, n_samples;
+  int bc_minus;        // BC type on the minus side (resolved: never 0)
   double p[3], nu[3], ref[3], rad;
   int64_t sample_off;  // offset of this curve's samples in the concatenated layout
 };
 
 struct ShapeDev {
   int kind, dim, K;
+  int newton_maxit;  // iteration cap of each stage of the level-set projection (200)
   double R, rt, amp, width;
   const double *a;  // device [K]
   const double *c;  // device [3K]
@@ -50,6 +52,7 @@ struct ShapeDev {
 // read-only view passed by value to kernels
 struct BandView {
   int dim;
+  int np1;  // interpolation stencil nodes per axis: p + 1 (4 cubic, 3 quadratic)
   double h, inv_h, rband;
   int64_t nb, NS, NC;
   const uint64_t *bmask;  // [nb*8]
@@ -69,6 +72,16 @@ struct WorkBuf {
 
 struct SolveWork;
 
+// launch shapes chosen by the autotuner (tune.cu); 0 means the default
+struct Tune {
+  int cells_xh[2][2] = {{0, 0}, {0, 0}};  // [FP32 / FP64][columns per lane - 1]: x passes of the cell gather
+  int cells_blocks_per_sm = 0;            // grid cap of the cell gather (blocks of 8 warps per SM)
+  int combine_warps_per_sm = 0;           // grid cap of the warp-per-row combine
+  int vec_blocks_per_sm = 0;              // blocks per SM of the Krylov vector kernels (1, 2 or 4)
+  int gather1_per_cell = 0;               // single right-hand side gather: 1 thread per cell, 0 per row
+  bool tuned = false;
+};
+
 // event-pair timing of operator products and a kernel-launch counter
 struct Profiler {
   bool on = false;
@@ -81,10 +94,16 @@ struct Profiler {
 
 struct cpm_ctx {
   cudaStream_t stream = nullptr;
+  int nsm = 152;                    // streaming multiprocessors of the device (queried at build)
+  // the solves run on an internal stream, joined to the caller's by events, so
+  // that their iteration groups can be captured and replayed as CUDA graphs
+  cudaStream_t istream = nullptr;
+  cudaEvent_t ev_join[2] = {nullptr, nullptr};
   // geometry
   ShapeDev shape{};
   double *d_shape_a = nullptr, *d_shape_c = nullptr;
   int dim = 3;
+  int p = 3;                        // interpolation degree: 3 (cubic) or 2 (quadratic)
   double h = 0, rband = 0;
   double shape_seed[3] = {0, 0, 0};
   // bricks
@@ -118,8 +137,10 @@ struct cpm_ctx {
   int32_t *d_bc_curve = nullptr;  // [NC]
   double *d_cpc = nullptr;        // [NC*3]
   int32_t *d_side = nullptr;      // [NC]
+  int32_t *d_bc_type = nullptr;   // [NC] BC type of the row (the side opposite cp_S(x_alpha))
   double *d_param = nullptr;      // [NC]
   int32_t *d_bc_cnt = nullptr;    // [NC]
+  int32_t *d_curve_first = nullptr;  // [ncurves+1] first BC DOF of each curve
   int32_t *d_bc_col = nullptr;    // [NC*65]
   double *d_bc_val = nullptr;     // [NC*65]
   float *d_bc_val32 = nullptr;    // [NC*65]
@@ -159,21 +180,21 @@ struct cpm_ctx {
   int32_t *d_T_kind = nullptr;      // [nT] 0: flipped FD entry, 1: flipped E entry, 2: BC-row entry
   double *d_T_val = nullptr;        // [nT]
   float *d_T_val32 = nullptr;       // [nT]
-  // scratch
-  WorkBuf a_scratch;                // E u intermediate
+  // scratch, reserved in cpm_set_boundary / cpm_reserve (the products and
+  // solves themselves allocate nothing)
+  WorkBuf a_scratch;                // E u intermediate (also the heat steps' extensions)
   WorkBuf b_scratch;                // transposed FD intermediate
-  WorkBuf heat_scratch;             // extended fields of the gradient / divergence
+  int64_t res_ld = 0;               // leading dimension the workspaces are reserved for
+  int res_flags = 0;                // solve forms reserved (CPM_RESERVE_* bits)
   unsigned *d_err = nullptr;        // device error flags
   unsigned long long *d_counter = nullptr;  // diagnostics counters [4]
   int64_t noflip_twin = 0;
   Profiler prof;
-  SolveWork *solve = nullptr;        // workspace of the solves (per precision form)
-  SolveWork *solve_adj = nullptr;
-  SolveWork *solve64 = nullptr;      // FP64 finishing phase of the FP32 form
-  SolveWork *solve_adj64 = nullptr;
+  Tune tune;
+  SolveWork *solve = nullptr;        // workspace of the solves (all forms share it)
   BandView view() const {
     BandView v;
-    v.dim = dim; v.h = h; v.inv_h = 1.0 / h; v.rband = rband;
+    v.dim = dim; v.np1 = p + 1; v.h = h; v.inv_h = 1.0 / h; v.rband = rband;
     v.nb = nb; v.NS = NS; v.NC = NC;
     v.bmask = d_bmask; v.brank = d_brank; v.bstart = d_bstart; v.bnbr = d_bnbr;
     v.hkeys = d_hkeys; v.slot_to_sorted = d_slot_to_sorted; v.hcap = hcap;
@@ -210,10 +231,14 @@ void cpm_free_cells(cpm_ctx *c);
   for (int64_t i = blockIdx.x * (int64_t)rows_per_ + threadIdx.x / (unsigned)(nrhs); i < (N); \
        i += (int64_t)gridDim.x * rows_per_)
 
+// SM count of the current device (queried once per device)
+int cpm_device_sms();
+
 static inline unsigned cpm_grid(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   if (g < 1) g = 1;
-  if (g > 152 * 64) g = 152 * 64;  // grid-stride loops beyond this
+  const int64_t cap = (int64_t)cpm_device_sms() * 64;  // grid-stride loops beyond this
+  if (g > cap) g = cap;
   return (unsigned)g;
 }
 
@@ -339,14 +364,29 @@ __device__ __forceinline__ void cpm_cp_C(const CurveDev &cv, const double *x, do
   out[2] = rn_add(cv.p[2], rn_mul(cv.rad, rn_div(q[2], nq)));
 }
 
-// stencil base node floor(y/h) - 1 and t = y/h - base per axis
-__device__ __forceinline__ void cpm_stencil_of(int dim, double h, const double *y, int base[3], double t[3]) {
+// stencil of a query point y: the np1 = p + 1 nodes per axis nearest to y.
+// Cubic: base floor(y/h) - 1 (y between stencil nodes 1 and 2); quadratic:
+// base floor(y/h + 1/2) - 1 (node 1 nearest, every node within 1.5 h, the
+// half-width Eq. (3) assumes).  t = y/h - base per axis.
+__device__ __forceinline__ void cpm_stencil_of(int dim, double h, int np1, const double *y, int base[3],
+                                               double t[3]) {
   for (int a = 0; a < 3; ++a) {
     if (a >= dim) { base[a] = 0; t[a] = 0.0; continue; }
     double s = rn_div(y[a], h);
-    base[a] = (int)floor(s) - 1;
+    base[a] = (np1 == 3) ? (int)floor(rn_add(s, 0.5)) - 1 : (int)floor(s) - 1;
     t[a] = rn_sub(s, (double)base[a]);
   }
+}
+
+// entry e of a stencil in the fixed 4 x 4 x 4 layout (x fastest) lies inside
+// the np1^dim stencil
+__host__ __device__ inline bool cpm_in_stencil(int e, int np1, int dim) {
+  return (e & 3) < np1 && ((e >> 2) & 3) < np1 && (dim == 3 ? (e >> 4) < np1 : (e >> 4) == 0);
+}
+
+// c_alpha of the BC-row right-hand side: 1 (DIR1), 2 (DIR2), 0 (zero-Neumann)
+__host__ __device__ inline double cpm_bc_data_scale(int type) {
+  return (type == CPM_BC_DIR1) ? 1.0 : (type == CPM_BC_DIR2) ? 2.0 : 0.0;
 }
 
 // 1D cubic Lagrange weights on nodes 0..3 (product form)
@@ -357,4 +397,26 @@ __device__ __forceinline__ void cpm_lagrange4(T t, T w[4]) {
   w[1] = (a * c * d) * T(0.5);
   w[2] = -(a * b * d) * T(0.5);
   w[3] = (a * b * c) * T(1.0 / 6.0);
+}
+
+// 1D quadratic Lagrange weights on nodes 0..2 (product form)
+template <typename T>
+__device__ __forceinline__ void cpm_lagrange3(T t, T w[3]) {
+  T a = t, b = t - T(1), c = t - T(2);
+  w[0] = (b * c) * T(0.5);
+  w[1] = -(a * c);
+  w[2] = (a * b) * T(0.5);
+}
+
+template <int NP, typename T>
+__device__ __forceinline__ void cpm_lagrange(T t, T *w) {
+  if constexpr (NP == 4) cpm_lagrange4<T>(t, w);
+  else cpm_lagrange3<T>(t, w);
+}
+
+// run-time degree: weights in w[0..np1), zeros after
+template <typename T>
+__device__ __forceinline__ void cpm_lagrange_rt(int np1, T t, T w[4]) {
+  if (np1 == 4) cpm_lagrange4<T>(t, w);
+  else { cpm_lagrange3<T>(t, w); w[3] = T(0); }
 }

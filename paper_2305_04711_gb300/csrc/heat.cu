@@ -59,10 +59,11 @@ __global__ void div_kernel(int64_t NS, int dim, double inv2h, const int32_t *nbr
 }  // namespace
 
 cpm_status cpm_internal_surface_gradient(cpm_ctx *c, const double *u, double *X, int normalize, cudaStream_t st) {
-  cpm_status rc = cpm_ensure(c->heat_scratch, sizeof(double) * (size_t)std::max<int64_t>(c->NS, 1));
-  if (rc) return rc;
-  double *a = reinterpret_cast<double *>(c->heat_scratch.p);
-  rc = cpm_internal_extend(c, u, a, 1, 1, st);
+  // the extension goes to the context's product scratch (reserved at set-up
+  // for at least 3 FP64 columns)
+  if (sizeof(double) * (size_t)c->NS > c->a_scratch.bytes) return CPM_ERR_CAPACITY;
+  double *a = reinterpret_cast<double *>(c->a_scratch.p);
+  cpm_status rc = cpm_internal_extend(c, u, a, 1, 1, st);
   if (rc) return rc;
   grad_kernel<<<cpm_grid(c->NS + c->NC, 256), 256, 0, st>>>(c->NS, c->NC, c->dim, 0.5 / c->h, c->d_nbr8, c->d_twin, a,
                                                             u, normalize, X);
@@ -72,10 +73,9 @@ cpm_status cpm_internal_surface_gradient(cpm_ctx *c, const double *u, double *X,
 }
 
 cpm_status cpm_internal_surface_divergence(cpm_ctx *c, const double *X, double *b, cudaStream_t st) {
-  cpm_status rc = cpm_ensure(c->heat_scratch, sizeof(double) * 3 * (size_t)std::max<int64_t>(c->NS, 1));
-  if (rc) return rc;
-  double *xe = reinterpret_cast<double *>(c->heat_scratch.p);
-  rc = cpm_internal_extend(c, X, xe, 3, 3, st);
+  if (sizeof(double) * 3 * (size_t)c->NS > c->a_scratch.bytes) return CPM_ERR_CAPACITY;
+  double *xe = reinterpret_cast<double *>(c->a_scratch.p);
+  cpm_status rc = cpm_internal_extend(c, X, xe, 3, 3, st);
   if (rc) return rc;
   div_kernel<<<cpm_grid(c->NS, 256), 256, 0, st>>>(c->NS, c->dim, 0.5 / c->h, c->d_nbr8, xe, X, b);
   cpm_count_launches(c, 2);

@@ -1,29 +1,44 @@
 // krylov.cu -- preconditioned BiCGSTAB on the device (Sec. 5.4), in FP64 or as
 // FP32 inner solves of a mixed-precision iterative refinement.
 //
-// The solver is van der Vorst's BiCGSTAB with the diagonal of m I + n diag(L)
+// The solver is van der Vorst's BiCGSTAB with the diagonal D of m I + n diag(L)
 // on PDE rows and 1 on BC rows as preconditioner (Sec. 5.4).  Two forms:
-//  * scaled (default): BiCGSTAB on the row-scaled system (W A) x = W f with W
-//    that diagonal's inverse, so the recursive residual is the Jacobi-scaled
-//    one, in which PDE rows (scale 1/h^2) and BC rows (scale 1) are comparable;
-//  * plain: the paper's right-preconditioned form with the unscaled residual.
-// All right-hand sides of a batch ([N][ld] layout) iterate together, each with
-// its own scalars (rho, alpha, omega) in device memory, so iterations run
-// without a host round trip; the host reads the per-column flags every
-// `check_every` iterations.  Dot products are deterministic: fixed-size block
-// partials reduced in a fixed order.  A right-hand side that reaches the
-// tolerance is frozen.  A near-zero rho restarts that right-hand side's shadow
-// residual (r_hat = r); too many restarts is a breakdown.
+//  * plain (default, the paper's): right-preconditioned, A D mu = f with
+//    x = D mu; the recursive residual is the unscaled f - A x, and the
+//    stopping test is |f - A x|_2 <= tol |f|_2 per right-hand side;
+//  * scaled: BiCGSTAB on the row-scaled system (W A) x = W f, W = D^-1, whose
+//    residual is the Jacobi-scaled one.
+// D never becomes a vector pass: the operator applies it as a column (right)
+// or row (left) factor of the PDE entries, and the solution update folds it in.
 //
-// The FP32 form is mixed-precision iterative refinement: the solution x and
-// the residual f - A x are FP64; each outer step solves for a correction with
-// FP32 BiCGSTAB (FP32 operator in its difference form and FP32 Krylov vectors,
-// the correction itself accumulated in FP64) and adds it to x.  Storing a
-// smooth field in FP32 limits the FP32 operator's relative accuracy to about
-// eps_32 / h^2 times the field-to-Laplacian ratio, so each outer step targets
-// a modest reduction (1e-2 by default) and starts a fresh Krylov space.
-// Convergence is decided on the FP64 residual only; a column that the FP32
-// steps stop improving finishes in FP64.
+// One iteration is five vector kernels and two operator products:
+//   p  = r + beta (p - omega v)            (shadow restart: rhat = w r, p = r)
+//   v  = A D p;  (rhat, v) -> alpha        (dot kernel, last block finishes)
+//   s  = r - alpha v
+//   t  = A D s;  (t, s), (t, t) -> omega
+//   x += D (alpha p + omega s);  r = s - omega t;
+//        (r, r), (rhat, r), (rhat, rhat), (w r, r) -> convergence, rho, beta
+// Every dot product is reduced deterministically: a fixed grid of blocks, each
+// reducing its rows in a fixed order (warp shuffles, then shared memory) to a
+// partial per right-hand side, and the last block to arrive (atomic ticket)
+// summing the partials in block order and updating the per-right-hand-side
+// scalars (rho, alpha, omega, beta, convergence flags) on the device.  The
+// iterations therefore need no host round trip; the host reads the flags every
+// `check_every` iterations, and on an internal stream replays those iteration
+// groups from a captured CUDA graph.  All right-hand sides of a batch ([N][ld]
+// layout) iterate together with their own scalars; a right-hand side that
+// converges is frozen.
+//
+// The FP32 form is mixed-precision iterative refinement by residual
+// replacement: FP32 BiCGSTAB (FP32 operator in its difference form, FP32
+// Krylov vectors) on the correction equation, its updates accumulated in the
+// FP64 solution; every time a column's FP32 residual has fallen by inner_tol
+// the FP64 residual f - A x replaces it, keeping the Krylov space (see
+// ir_reliable).  Convergence is decided on the FP64 residual only; a column
+// that stops gaining finishes in FP64.
+//
+// Workspaces are reserved by cpm_set_boundary / cpm_reserve; solves allocate
+// nothing.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -38,143 +53,34 @@
 
 namespace {
 
-constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs: fixed, so reductions are deterministic
-constexpr int RED_THREADS = 256;
-
-// partial sums of up to 3 dot products per column: part[blk][q][r];
-// products on PDE rows (i < NS) are weighted by wpde (1 for plain dot products)
+constexpr int KT = 512;    // threads per block of the vector kernels
+constexpr int NQMAX = 4;   // dot products reduced by one kernel at most
+// elements per thread in flight in the vector loops (16 bytes of each vector)
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) dots_kernel(const T *__restrict__ a0, const T *__restrict__ b0,
-                                                           const T *__restrict__ a1, const T *__restrict__ b1,
-                                                           const T *__restrict__ a2, const T *__restrict__ b2, int nq,
-                                                           int64_t N, int64_t NS, double wpde, int nrhs, int64_t ld,
-                                                           double *part) {
-  __shared__ double sh[3][RED_THREADS];
-  const int rows_per = RED_THREADS / nrhs;
-  const int t = threadIdx.x;
-  const int r = t % nrhs, sub = t / nrhs;
-  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
-  if (sub < rows_per) {
-    int64_t chunk = (N + gridDim.x - 1) / gridDim.x;
-    int64_t lo = blockIdx.x * chunk, hi = lo + chunk < N ? lo + chunk : N;
-    // runs of 16 products are summed in T, the runs in FP64 (for FP32 vectors
-    // this keeps the FP64 pipe, 1/64 of the FP32 rate here, off the hot loop)
-    for (int64_t i = lo + sub; i < hi;) {
-      T c0 = T(0), c1 = T(0), c2 = T(0);
-      for (int k = 0; k < 16 && i < hi; ++k, i += rows_per) {
-        const int64_t o = i * ld + r;
-        const T wi = (i < NS) ? T(wpde) : T(1);
-        c0 += wi * (a0[o] * b0[o]);
-        if (nq > 1) c1 += wi * (a1[o] * b1[o]);
-        if (nq > 2) c2 += wi * (a2[o] * b2[o]);
-      }
-      acc0 += (double)c0;
-      acc1 += (double)c1;
-      acc2 += (double)c2;
-    }
-  }
-  sh[0][t] = acc0; sh[1][t] = acc1; sh[2][t] = acc2;
-  __syncthreads();
-  if (t < nrhs) {
-    for (int q = 0; q < nq; ++q) {
-      double s = 0.0;
-      for (int k = 0; k < rows_per; ++k) s += sh[q][k * nrhs + t];
-      part[((int64_t)blockIdx.x * 3 + q) * nrhs + t] = s;
-    }
-  }
-}
+constexpr int unroll_of() { return (sizeof(T) == 8) ? 2 : 4; }
 
-__global__ void reduce_parts_kernel(const double *part, int nblocks, int nq, int nrhs, double *out) {
-  int t = threadIdx.x;
-  for (int qr = t; qr < nq * nrhs; qr += blockDim.x) {
-    int q = qr / nrhs, r = qr % nrhs;
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[((int64_t)b * 3 + q) * nrhs + r];
-    out[q * nrhs + r] = s;
-  }
-}
+// per right-hand side scalar slots
+enum {
+  S_RHO_OLD = 0, S_ALPHA, S_OMEGA, S_RHO, S_BETA, S_ACTIVE, S_RESTART, S_NRESTART, S_FN2, S_RN2, S_BROKE,
+  S_BEST, S_STALL, S_STOPPED, S_RN2_0, S_ITERS, NSC
+};
 
-// ---- per-RHS scalar state ---------------------------------------------------
-// sc layout per rhs r: [0] rho_old [1] alpha [2] omega [3] rho [4] beta
-//                      [5] active (1/0) [6] restart flag [7] restarts
-//                      [8] |W f|^2 [9] |r|^2 (recursive) [10] breakdown
-//                      [11] best |r|^2 [12] iterations since |r| last halved
-//                      [13] stopped without reaching tol (stall or divergence)
-//                      [14] |r|^2 at the start
-constexpr int NSC = 15;
+enum { ST_OUT = 0, ST_INIT, ST_ALPHA, ST_OMEGA, ST_XR, ST_REPL };
 
-__global__ void scal_init_kernel(double *sc, const double *dots /* (r,r),(f,f) */, int nrhs, double tol) {
-  int r = threadIdx.x;
-  if (r >= nrhs) return;
-  double *s = sc + r * NSC;
-  s[0] = 1.0; s[1] = 1.0; s[2] = 1.0; s[3] = 0.0; s[4] = 0.0;
-  s[6] = 0.0; s[7] = 0.0; s[10] = 0.0; s[12] = 0.0; s[13] = 0.0;
-  double fn2 = dots[nrhs + r];
-  s[8] = fn2 > 0.0 ? fn2 : 1.0;
-  s[9] = dots[r];
-  s[11] = s[9];
-  s[14] = s[9];
-  s[5] = (sqrt(s[9]) <= tol * sqrt(s[8]) || !isfinite(s[9])) ? 0.0 : 1.0;
-}
+struct Red {
+  double *part;      // [G][NQMAX][nrhs] block partials
+  unsigned *ticket;  // arrival counter (reset by the last block)
+  double *sc;        // [nrhs][NSC]
+  double *out;       // [NQMAX][nrhs] reduced dot products (ST_OUT / ST_INIT)
+  const double *flag;  // [nrhs] per-column selection (ST_REPL)
+  int nrhs;
+};
 
-// after dots (rhat, r), (rhat, rhat): rho, beta, restart decision
-__global__ void scal_rho_kernel(double *sc, const double *dots, int nrhs) {
-  int r = threadIdx.x;
-  if (r >= nrhs) return;
-  double *s = sc + r * NSC;
-  if (s[5] == 0.0) return;
-  double rho = dots[r], rhn2 = dots[nrhs + r];
-  s[6] = 0.0;
-  if (fabs(rho) <= 1e-28 * sqrt(rhn2) * sqrt(s[9]) || rho == 0.0) {
-    // restart the shadow residual: rhat = r, rho = (r, r), p = r
-    s[6] = 1.0;
-    s[7] += 1.0;
-    if (s[7] > 20.0) { s[10] = 1.0; s[5] = 0.0; return; }
-    rho = s[9];
-    s[0] = 1.0; s[1] = 1.0; s[2] = 1.0;
-  }
-  s[4] = (rho / s[0]) * (s[1] / s[2]);
-  s[3] = rho;
-}
-
-__global__ void scal_alpha_kernel(double *sc, const double *dots, int nrhs) {
-  int r = threadIdx.x;
-  if (r >= nrhs) return;
-  double *s = sc + r * NSC;
-  if (s[5] == 0.0) return;
-  double d = dots[r];
-  if (d == 0.0 || !isfinite(d)) { s[10] = 1.0; s[5] = 0.0; return; }
-  s[1] = s[3] / d;
-}
-
-__global__ void scal_omega_kernel(double *sc, const double *dots, int nrhs) {
-  int r = threadIdx.x;
-  if (r >= nrhs) return;
-  double *s = sc + r * NSC;
-  if (s[5] == 0.0) return;
-  double ts = dots[r], tt = dots[nrhs + r];
-  s[2] = (tt > 0.0) ? ts / tt : 0.0;
-  if (s[2] == 0.0) { s[10] = 1.0; s[5] = 0.0; }
-}
-
-// after (r, r): convergence on the recursive residual (decide == 1) or only
-// bookkeeping (decide == 0: the FP64 residual decides, FP32 form)
-__global__ void scal_conv_kernel(double *sc, const double *dots, int nrhs, double tol, double stall, int decide) {
-  int r = threadIdx.x;
-  if (r >= nrhs) return;
-  double *s = sc + r * NSC;
-  if (s[5] == 0.0) return;
-  s[9] = dots[r];
-  s[0] = s[3];
-  if (!isfinite(s[9]) || s[9] > 1e16 * s[11]) { s[13] = 1.0; s[5] = 0.0; return; }
-  if (decide && sqrt(s[9]) <= tol * sqrt(s[8])) { s[5] = 0.0; return; }
-  if (s[9] < 0.25 * s[11]) { s[11] = s[9]; s[12] = 0.0; }
-  else { s[12] += 1.0; if (decide && s[12] > stall) { s[13] = 1.0; s[5] = 0.0; } }
-}
-
-// ---- fused vector updates ---------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T dinv_of(int64_t i, int64_t NS, T dS) { return (i < NS) ? dS : T(1); }
+struct Conv {
+  double tol;    // relative tolerance on the iterated system's residual
+  double stall;  // iterations without the residual halving before giving up
+  float mix;     // shadow-residual perturbation (0: rhat = r)
+};
 
 // shadow-residual weight 1 + mix * u(i, c), u a fixed hash in [-1, 1]: with mix
 // in [0, 1) it keeps (rhat, r) > 0 while breaking the structure that drives
@@ -187,76 +93,438 @@ __device__ __forceinline__ float shadow_weight(int64_t i, int c, float mix) {
   return 1.0f + mix * u;
 }
 
-// p = restart ? r : r + beta (p - omega v);  ph = D p;  (restart: rhat = r)
-template <typename T>
-__global__ void upd_p_kernel(const double *sc, int64_t N, int64_t NS, int nrhs, int64_t ld, T dS, float mix,
-                             const T *r, T *rh, T *p, const T *v, T *ph) {
-  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
-    const double *s = sc + c * NSC;
-    if (s[5] == 0.0) continue;
-    int64_t o = i * ld + c;
-    T pv;
-    if (s[6] != 0.0) {
-      rh[o] = r[o] * T(shadow_weight(i, c, mix));
-      pv = r[o];
-    } else {
-      pv = r[o] + T(s[4]) * (p[o] - T(s[2]) * v[o]);
+// ---- deterministic block reduction -----------------------------------------
+// Thread t of a block owns column c = t % nrhs and rows sub, sub + rows_per,
+// ... of the block's share (sub = t / nrhs, rows_per = KT / nrhs).
+template <int NQ>
+__device__ __forceinline__ bool block_publish(const double (&acc)[NQ], const Red &R) {
+  __shared__ double sh[NQ][KT];
+  __shared__ bool s_last;
+  const int t = threadIdx.x, nrhs = R.nrhs;
+  if (nrhs < 32 && (32 % nrhs) == 0) {
+    // lanes with equal column combine by xor shuffles, then the warps in order
+    double v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = acc[q];
+    for (int off = 16; off >= nrhs; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+    const int lane = t & 31, w = t >> 5;
+    if (lane < nrhs)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) sh[q][w * nrhs + lane] = v[q];
+    __syncthreads();
+    if (t < nrhs)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        double s = 0.0;
+        for (int k = 0; k < KT / 32; ++k) s += sh[q][k * nrhs + t];
+        R.part[((int64_t)blockIdx.x * NQMAX + q) * nrhs + t] = s;
+      }
+  } else {
+    const int rows_per = KT / nrhs;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sh[q][t] = acc[q];
+    __syncthreads();
+    if (t < nrhs)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        double s = 0.0;
+        for (int k = 0; k < rows_per; ++k) s += sh[q][k * nrhs + t];
+        R.part[((int64_t)blockIdx.x * NQMAX + q) * nrhs + t] = s;
+      }
+  }
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = (atomicAdd(R.ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  return s_last;
+}
+
+__device__ void stage_finish(int stage, const Red &R, const Conv &cv, int c, const double *d) {
+  double *s = R.sc + c * NSC;
+  if (stage == ST_OUT) return;
+  if (stage == ST_INIT) {
+    const double fn2 = d[1] > 0.0 ? d[1] : 1.0;
+    s[S_FN2] = fn2;
+    s[S_RN2] = d[0]; s[S_BEST] = d[0]; s[S_RN2_0] = d[0];
+    s[S_RHO] = d[0]; s[S_RHO_OLD] = 1.0; s[S_ALPHA] = 1.0; s[S_OMEGA] = 1.0; s[S_BETA] = 0.0;
+    s[S_RESTART] = 0.0; s[S_NRESTART] = 0.0; s[S_BROKE] = 0.0; s[S_STALL] = 0.0; s[S_STOPPED] = 0.0;
+    s[S_ITERS] = 0.0;
+    const bool fin = isfinite(d[0]);
+    s[S_ACTIVE] = (!fin || sqrt(d[0]) <= cv.tol * sqrt(fn2)) ? 0.0 : 1.0;
+    if (!fin) s[S_STOPPED] = 1.0;
+    return;
+  }
+  if (stage == ST_REPL) {
+    // residual replacement of a column whose recursion reached its reduction
+    // target: r now holds the (scaled) FP64 residual; the search direction p
+    // and the shadow residual stay, rho and beta follow the new r
+    if (R.flag[c] == 0.0) return;
+    double rho = d[0];
+    s[S_RESTART] = 0.0;
+    if (fabs(rho) <= 1e-28 * sqrt(d[2]) * sqrt(d[1]) || rho == 0.0) {
+      s[S_RESTART] = 1.0;
+      s[S_NRESTART] += 1.0;
+      rho = (cv.mix != 0.0f) ? d[3] : d[1];
+      s[S_RHO] = 1.0; s[S_ALPHA] = 1.0; s[S_OMEGA] = 1.0;
     }
-    p[o] = pv;
-    if (ph != p) ph[o] = dinv_of<T>(i, NS, dS) * pv;
+    double beta = (rho / s[S_RHO]) * (s[S_ALPHA] / s[S_OMEGA]);
+    if (!isfinite(beta) || s[S_BROKE] != 0.0) {
+      // the recursion broke down before: restart the Krylov space from r
+      s[S_RESTART] = 1.0;
+      rho = (cv.mix != 0.0f) ? d[3] : d[1];
+      s[S_RHO] = 1.0; s[S_ALPHA] = 1.0; s[S_OMEGA] = 1.0;
+      beta = 0.0;
+      s[S_BROKE] = 0.0;
+    }
+    s[S_BETA] = beta;
+    s[S_RHO_OLD] = s[S_RHO];
+    s[S_RHO] = rho;
+    s[S_FN2] = d[1] > 0.0 ? d[1] : 1.0;
+    s[S_RN2] = d[1]; s[S_BEST] = d[1]; s[S_STALL] = 0.0; s[S_STOPPED] = 0.0;
+    s[S_ACTIVE] = (d[1] > 0.0 && isfinite(d[1])) ? 1.0 : 0.0;
+    return;
   }
+  if (s[S_ACTIVE] == 0.0) return;
+  if (stage == ST_ALPHA) {
+    if (d[0] == 0.0 || !isfinite(d[0])) { s[S_BROKE] = 1.0; s[S_ACTIVE] = 0.0; return; }
+    s[S_ALPHA] = s[S_RHO] / d[0];
+    return;
+  }
+  if (stage == ST_OMEGA) {
+    const double om = (d[1] > 0.0) ? d[0] / d[1] : 0.0;
+    s[S_OMEGA] = om;
+    if (om == 0.0 || !isfinite(om)) { s[S_BROKE] = 1.0; s[S_ACTIVE] = 0.0; }
+    return;
+  }
+  // ST_XR: residual bookkeeping, then rho and beta of the next iteration
+  s[S_ITERS] += 1.0;
+  const double rn2 = d[0];
+  s[S_RN2] = rn2;
+  if (!isfinite(rn2) || rn2 > 1e16 * s[S_BEST]) { s[S_STOPPED] = 1.0; s[S_ACTIVE] = 0.0; return; }
+  if (sqrt(rn2) <= cv.tol * sqrt(s[S_FN2])) { s[S_ACTIVE] = 0.0; return; }
+  if (rn2 < 0.25 * s[S_BEST]) { s[S_BEST] = rn2; s[S_STALL] = 0.0; }
+  else {
+    s[S_STALL] += 1.0;
+    if (s[S_STALL] > cv.stall) { s[S_STOPPED] = 1.0; s[S_ACTIVE] = 0.0; return; }
+  }
+  double rho = d[1];
+  s[S_RESTART] = 0.0;
+  if (fabs(rho) <= 1e-28 * sqrt(d[2]) * sqrt(rn2) || rho == 0.0) {
+    // restart the shadow residual: rhat = w r, p = r, rho = (w r, r)
+    s[S_RESTART] = 1.0;
+    s[S_NRESTART] += 1.0;
+    if (s[S_NRESTART] > 20.0) { s[S_BROKE] = 1.0; s[S_ACTIVE] = 0.0; return; }
+    rho = (cv.mix != 0.0f) ? d[3] : rn2;
+    s[S_RHO] = 1.0; s[S_ALPHA] = 1.0; s[S_OMEGA] = 1.0;
+  }
+  s[S_BETA] = (rho / s[S_RHO]) * (s[S_ALPHA] / s[S_OMEGA]);
+  s[S_RHO_OLD] = s[S_RHO];
+  s[S_RHO] = rho;
 }
 
-// s = r - alpha v;  sh = D s
+// the last block: sum the partials in block order (a warp per (q, c), lanes
+// strided over the blocks, then an xor-shuffle tree, identical in every lane)
+template <int NQ>
+__device__ void finish_reduce(int stage, const Red &R, const Conv &cv) {
+  __shared__ double sd[NQMAX][256];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nrhs = R.nrhs;
+  const int G = gridDim.x;
+  __threadfence();
+  for (int pr = w; pr < NQ * nrhs; pr += KT / 32) {
+    const int q = pr / nrhs, c = pr - q * nrhs;
+    double s = 0.0;
+    for (int b = lane; b < G; b += 32) s += __ldcg(R.part + ((int64_t)b * NQMAX + q) * nrhs + c);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) sd[q][c] = s;
+  }
+  __syncthreads();
+  if (t < nrhs) {
+    double d[NQMAX] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) d[q] = sd[q][t];
+    if (stage == ST_OUT || stage == ST_INIT)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) R.out[q * nrhs + t] = d[q];
+    stage_finish(stage, R, cv, t, d);
+  }
+  if (t == 0) *R.ticket = 0u;
+}
+
+// grid-stride element loop with UNR elements per thread in flight; the body
+// functor loads into its element state, then updates and accumulates.  Runs
+// of 16 products are summed in T, the runs in FP64 (for FP32 vectors this
+// keeps the FP64 pipe, 1/64 of the FP32 rate here, off the hot loop).
+template <typename T, int NQ, class Body>
+__device__ __forceinline__ void vloop(const Body &body, int64_t N, int nrhs, int64_t ld, double (&acc)[NQ]) {
+  constexpr int UNR = unroll_of<T>();
+  const int c = threadIdx.x % nrhs, sub = threadIdx.x / nrhs, rows_per = KT / nrhs;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  if (sub >= rows_per || !body.on(c)) return;
+  body.init(c);
+  const int64_t stride = (int64_t)gridDim.x * rows_per;
+  T run[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) run[q] = T(0);
+  int k = 0;
+  for (int64_t i0 = (int64_t)blockIdx.x * rows_per + sub; i0 < N; i0 += UNR * stride) {
+    typename Body::Elt e[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < N) body.load(e[u], i, i * ld + c);
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < N) body.apply(e[u], i, i * ld + c, run);
+    }
+    k += UNR;
+    if (k >= 16) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) { acc[q] += (double)run[q]; run[q] = T(0); }
+      k = 0;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] += (double)run[q];
+}
+
+// ---- iteration kernels -------------------------------------------------------
 template <typename T>
-__global__ void upd_s_kernel(const double *sc, int64_t N, int64_t NS, int nrhs, int64_t ld, T dS, const T *r,
-                             const T *v, T *s_, T *sh) {
-  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
-    const double *s = sc + c * NSC;
-    if (s[5] == 0.0) continue;
-    int64_t o = i * ld + c;
-    T sv = r[o] - T(s[1]) * v[o];
-    s_[o] = sv;
-    if (sh != s_) sh[o] = dinv_of<T>(i, NS, dS) * sv;
+struct PBody {
+  const double *sc; float mix;
+  const T *__restrict__ r; T *__restrict__ rh; T *__restrict__ p; const T *__restrict__ v;
+  mutable int c_; mutable bool restart; mutable T beta, omega;
+  struct Elt { T r, p, v; };
+  __device__ bool on(int c) const { return sc[c * NSC + S_ACTIVE] != 0.0; }
+  __device__ void init(int c) const {
+    c_ = c;
+    restart = sc[c * NSC + S_RESTART] != 0.0;
+    beta = T(sc[c * NSC + S_BETA]);
+    omega = T(sc[c * NSC + S_OMEGA]);
   }
+  __device__ void load(Elt &e, int64_t, int64_t o) const {
+    e.r = r[o];
+    if (!restart) { e.p = p[o]; e.v = v[o]; }
+  }
+  __device__ void apply(Elt &e, int64_t i, int64_t o, T (&)[1]) const {
+    if (restart) {
+      rh[o] = e.r * T(shadow_weight(i, c_, mix));
+      p[o] = e.r;
+    } else {
+      p[o] = e.r + beta * (e.p - omega * e.v);
+    }
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(KT, 2) kp_kernel(const double *sc, float mix, int64_t N, int nrhs, int64_t ld,
+                                                const T *r, T *rh, T *p, const T *v) {
+  PBody<T> b{sc, mix, r, rh, p, v};
+  double acc[1];
+  vloop<T, 1>(b, N, nrhs, ld, acc);
 }
 
-// x += alpha ph + omega sh;  r = s - omega t
-// (x may be kept in a wider type TX than the Krylov vectors: the increment is
-// formed in T and accumulated in TX)
+template <typename T>
+struct SBody {
+  const double *sc;
+  const T *__restrict__ r; const T *__restrict__ v; T *__restrict__ s;
+  mutable T alpha;
+  struct Elt { T r, v; };
+  __device__ bool on(int c) const { return sc[c * NSC + S_ACTIVE] != 0.0; }
+  __device__ void init(int c) const { alpha = T(sc[c * NSC + S_ALPHA]); }
+  __device__ void load(Elt &e, int64_t, int64_t o) const { e.r = r[o]; e.v = v[o]; }
+  __device__ void apply(Elt &e, int64_t, int64_t o, T (&)[1]) const { s[o] = e.r - alpha * e.v; }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(KT, 2) ks_kernel(const double *sc, int64_t N, int nrhs, int64_t ld, const T *r,
+                                                const T *v, T *s) {
+  SBody<T> b{sc, r, v, s};
+  double acc[1];
+  vloop<T, 1>(b, N, nrhs, ld, acc);
+}
+
+// (a, b) [and (a, a)] with a stage finish
+template <typename T, int NQ>
+struct DotBody {
+  const double *sc;
+  const T *__restrict__ a; const T *__restrict__ b;
+  struct Elt { T a, b; };
+  __device__ bool on(int c) const { return sc == nullptr || sc[c * NSC + S_ACTIVE] != 0.0; }
+  __device__ void init(int) const {}
+  __device__ void load(Elt &e, int64_t, int64_t o) const { e.a = a[o]; if (NQ > 1 || b != a) e.b = b[o]; else e.b = e.a; }
+  __device__ void apply(Elt &e, int64_t, int64_t, T (&run)[NQ]) const {
+    run[0] += e.a * e.b;
+    if (NQ > 1) run[NQ - 1] += e.a * e.a;
+  }
+};
+
+template <typename T, int NQ>
+__global__ void __launch_bounds__(KT, 2) dot_kernel(Red R, Conv cv, int stage, int64_t N, int64_t ld, const T *a,
+                                                 const T *b) {
+  DotBody<T, NQ> body{R.sc, a, b};
+  double acc[NQ];
+  vloop<T, NQ>(body, N, R.nrhs, ld, acc);
+  if (block_publish<NQ>(acc, R)) finish_reduce<NQ>(stage, R, cv);
+}
+
+// x += D (alpha p + omega s);  r = s - omega t;  the XR dot products
 template <typename T, typename TX>
-__global__ void upd_xr_kernel(const double *sc, int64_t N, int nrhs, int64_t ld, TX *x, T *r, const T *ph,
-                              const T *sh, const T *s_, const T *t) {
-  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
-    const double *s = sc + c * NSC;
-    if (s[5] == 0.0) continue;
-    int64_t o = i * ld + c;
-    T al = T(s[1]), om = T(s[2]);
-    x[o] = x[o] + TX(al * ph[o] + om * sh[o]);
-    r[o] = s_[o] - om * t[o];
+struct XRBody {
+  const double *sc; float mix; int64_t NS; T cs;
+  TX *__restrict__ x; T *__restrict__ r; const T *__restrict__ rh; const T *__restrict__ p;
+  const T *__restrict__ s; const T *__restrict__ t;
+  mutable int c_; mutable T alpha, omega;
+  struct Elt { TX x; T rh, p, s, t; };
+  __device__ bool on(int c) const { return sc[c * NSC + S_ACTIVE] != 0.0; }
+  __device__ void init(int c) const {
+    c_ = c;
+    alpha = T(sc[c * NSC + S_ALPHA]);
+    omega = T(sc[c * NSC + S_OMEGA]);
   }
+  __device__ void load(Elt &e, int64_t, int64_t o) const {
+    e.x = x[o]; e.rh = rh[o]; e.p = p[o]; e.s = s[o]; e.t = t[o];
+  }
+  __device__ void apply(Elt &e, int64_t i, int64_t o, T (&run)[4]) const {
+    const T d = (i < NS) ? cs : T(1);
+    x[o] = e.x + TX(d * (alpha * e.p + omega * e.s));
+    const T rn = e.s - omega * e.t;
+    r[o] = rn;
+    run[0] += rn * rn;
+    run[1] += e.rh * rn;
+    run[2] += e.rh * e.rh;
+    if (mix != 0.0f) run[3] += T(shadow_weight(i, c_, mix)) * rn * rn;
+  }
+};
+
+template <typename T, typename TX>
+__global__ void __launch_bounds__(KT, 2) kxr_kernel(Red R, Conv cv, int64_t N, int64_t NS, T cs, int64_t ld, TX *x,
+                                                 T *r, const T *rh, const T *p, const T *s, const T *t) {
+  XRBody<T, TX> body{R.sc, cv.mix, NS, cs, x, r, rh, p, s, t};
+  double acc[4];
+  vloop<T, 4>(body, N, R.nrhs, ld, acc);
+  if (block_publish<4>(acc, R)) finish_reduce<4>(ST_XR, R, cv);
 }
 
-// r = f - r (r holds A x);  rhat = r;  p = v = 0
+// r = f - r (r holds A x, or nothing when x = 0);  rhat = r;  p = v = 0;
+// (r, r), (f, f) -> the initial scalars
 template <typename T>
-__global__ void init_r_kernel(int64_t N, int nrhs, int64_t ld, const T *f, T *r, T *rh, T *p, T *v) {
-  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
-    int64_t o = i * ld + c;
-    T rv = f[o] - r[o];
+struct InitBody {
+  const T *__restrict__ f; T *__restrict__ r; T *__restrict__ rh; T *__restrict__ p; T *__restrict__ v;
+  bool x_zero;
+  struct Elt { T f, r; };
+  __device__ bool on(int) const { return true; }
+  __device__ void init(int) const {}
+  __device__ void load(Elt &e, int64_t, int64_t o) const { e.f = f[o]; e.r = x_zero ? T(0) : r[o]; }
+  __device__ void apply(Elt &e, int64_t, int64_t o, T (&run)[2]) const {
+    const T rv = e.f - e.r;
+    r[o] = rv; rh[o] = rv; p[o] = T(0); v[o] = T(0);
+    run[0] += rv * rv;
+    run[1] += e.f * e.f;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(KT, 2) init_kernel(Red R, Conv cv, int64_t N, int64_t ld, bool x_zero, const T *f,
+                                                  T *r, T *rh, T *p, T *v) {
+  InitBody<T> body{f, r, rh, p, v, x_zero};
+  double acc[2];
+  vloop<T, 2>(body, N, R.nrhs, ld, acc);
+  if (block_publish<2>(acc, R)) finish_reduce<2>(ST_INIT, R, cv);
+}
+
+// ---- FP64 residual -----------------------------------------------------------
+// r = f - r (r holds A x) and the weighted norms |W r|^2, |W f|^2 with W = wrow
+// on PDE rows and 1 on BC rows
+struct ResidBody {
+  const double *__restrict__ f; double *__restrict__ r; int64_t NS; double w2;
+  struct Elt { double f, r; };
+  __device__ bool on(int) const { return true; }
+  __device__ void init(int) const {}
+  __device__ void load(Elt &e, int64_t, int64_t o) const { e.f = f[o]; e.r = r[o]; }
+  __device__ void apply(Elt &e, int64_t i, int64_t o, double (&run)[2]) const {
+    const double rv = e.f - e.r;
     r[o] = rv;
-    rh[o] = rv;
-    p[o] = T(0);
-    v[o] = T(0);
+    const double w = (i < NS) ? w2 : 1.0;
+    run[0] += w * (rv * rv);
+    run[1] += w * (e.f * e.f);
+  }
+};
+
+__global__ void __launch_bounds__(KT, 2) resid_kernel(Red R, int64_t N, int64_t NS, double w2, int64_t ld,
+                                                   const double *f, double *r) {
+  ResidBody body{f, r, NS, w2};
+  double acc[2];
+  vloop<double, 2>(body, N, R.nrhs, ld, acc);
+  Conv cv{0.0, 0.0, 0.0f};
+  if (block_publish<2>(acc, R)) finish_reduce<2>(ST_OUT, R, cv);
+}
+
+// y = x o xi with xi(i, c) = +-1 from a fixed hash: the model of the rounding
+// of x to FP64 (independent relative perturbations of each entry)
+__global__ void sign_perturb_kernel(int64_t N, int nrhs, int64_t ld, const double *x, double *y) {
+  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
+    uint64_t k = (uint64_t)i * 0x9E3779B97F4A7C15ull + (uint64_t)c * 0xD1B54A32D192ED03ull + 0x2545F4914F6CDD1Dull;
+    k ^= k >> 31; k *= 0xBF58476D1CE4E5B9ull; k ^= k >> 29;
+    const int64_t o = i * ld + c;
+    y[o] = ((k >> 40) & 1ull) ? x[o] : -x[o];
   }
 }
 
-// ---- FP64 pieces ------------------------------------------------------------
-// r = f - r (r holds A x)
-__global__ void residual64_kernel(int64_t N, int nrhs, int64_t ld, const double *f, double *r) {
-  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
-    int64_t o = i * ld + c;
-    r[o] = f[o] - r[o];
+// |W y|^2 per column (W = wrow on PDE rows, 1 on BC rows)
+struct WNormBody {
+  const double *__restrict__ y; int64_t NS; double w2;
+  struct Elt { double y; };
+  __device__ bool on(int) const { return true; }
+  __device__ void init(int) const {}
+  __device__ void load(Elt &e, int64_t, int64_t o) const { e.y = y[o]; }
+  __device__ void apply(Elt &e, int64_t i, int64_t, double (&run)[1]) const {
+    run[0] += ((i < NS) ? w2 : 1.0) * (e.y * e.y);
   }
+};
+
+__global__ void __launch_bounds__(KT, 2) wnorm_kernel(Red R, int64_t N, int64_t NS, double w2, int64_t ld,
+                                                      const double *y) {
+  WNormBody body{y, NS, w2};
+  double acc[1];
+  vloop<double, 1>(body, N, R.nrhs, ld, acc);
+  Conv cv{0.0, 0.0, 0.0f};
+  if (block_publish<1>(acc, R)) finish_reduce<1>(ST_OUT, R, cv);
+}
+
+// residual replacement: r = (float) (W r64) on the selected columns (W = wrow
+// on PDE rows, 1 on BC rows); (rhat, r), (r, r), (rhat, rhat), (w r, r)
+template <typename T>
+struct ReplBody {
+  const double *flag; const double *__restrict__ r64; T *__restrict__ r; const T *__restrict__ rh;
+  int64_t NS; double wrow; float mix;
+  mutable int c_;
+  struct Elt { double r64; T rh; };
+  __device__ bool on(int c) const { return flag[c] != 0.0; }
+  __device__ void init(int c) const { c_ = c; }
+  __device__ void load(Elt &e, int64_t, int64_t o) const { e.r64 = r64[o]; e.rh = rh[o]; }
+  __device__ void apply(Elt &e, int64_t i, int64_t o, T (&run)[4]) const {
+    const T rv = T(((i < NS) ? wrow : 1.0) * e.r64);
+    r[o] = rv;
+    run[0] += e.rh * rv;
+    run[1] += rv * rv;
+    run[2] += e.rh * e.rh;
+    if (mix != 0.0f) run[3] += T(shadow_weight(i, c_, mix)) * rv * rv;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(KT, 2) repl_kernel(Red R, Conv cv, int64_t N, int64_t NS, double wrow, int64_t ld,
+                                                     const double *r64, T *r, const T *rh) {
+  ReplBody<T> body{R.flag, r64, r, rh, NS, wrow, cv.mix};
+  double acc[4];
+  vloop<T, 4>(body, N, R.nrhs, ld, acc);
+  if (block_publish<4>(acc, R)) finish_reduce<4>(ST_REPL, R, cv);
 }
 
 // out = W f (PDE rows scaled by dS)
@@ -300,294 +568,433 @@ __global__ void ir_candidate_kernel(int64_t N, int nrhs, int64_t ld, const doubl
 }  // namespace
 
 // ---------------------------------------------------------------------------
-struct SolveWork {
-  cpm_ctx *owner = nullptr;  // for launch counting
-  int nrhs = 0;
+struct GraphKey {
+  const void *fn = nullptr;
+  double m = 0, n = 0, rs = 0, cs = 0, tol = 0, stall = 0;
+  float mix = 0;
+  const void *x = nullptr, *vecs = nullptr;
+  int nrhs = 0, steps = 0, elem = 0, xelem = 0, G = 0;
   int64_t ld = 0;
-  int elem = 0;  // bytes per element of the Krylov vectors
-  void *vec[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  double *r64 = nullptr;    // FP64 true residual
-  double *fs = nullptr;     // W f (scaled FP64 form)
-  float *f32 = nullptr;     // FP32 right-hand side of the inner solves
-  double *xd = nullptr;     // FP64 solution of the inner solves
-  double *part = nullptr, *dots = nullptr, *sc = nullptr;
-  double *h_pinned = nullptr;  // host mirror of sc
-  double *d_cols = nullptr;    // per-column host-set arrays: [4][nrhs]
+  bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+
+struct SolveWork {
+  int64_t N = 0, ld = 0;     // reserved rows and leading dimension
+  bool has32 = false;
+  double *v64[6] = {};       // FP64 Krylov vectors (FP64 solves, FP64 finish of FP32_IR)
+  float *v32[6] = {};        // FP32 Krylov vectors (FP32_IR inner solves)
+  double *r64 = nullptr;     // FP64 residual
+  double *xc = nullptr;      // FP32_IR candidate iterate
+  double *xd = nullptr;      // FP32_IR FP64 accumulator of the inner solution
+  double *part = nullptr, *sc = nullptr, *out = nullptr, *cols = nullptr;
+  unsigned *ticket = nullptr;
+  double *h_pin = nullptr;   // host mirror: [NSC * ld] scalars, then [NQMAX * ld] dots
+  int G = 0;                 // blocks of the vector kernels (fixed: deterministic reductions)
+  cudaGraphExec_t gexec = nullptr;
+  GraphKey gkey;
+  int64_t glaunches = 0;     // kernels per replay
+  bool graphs_ok = true;
 };
 
 static void free_work(SolveWork *w) {
   if (!w) return;
-  for (auto &p : w->vec) cudaFree(p);
-  cudaFree(w->r64); cudaFree(w->fs); cudaFree(w->f32); cudaFree(w->xd);
-  cudaFree(w->part); cudaFree(w->dots); cudaFree(w->sc); cudaFree(w->d_cols);
-  if (w->h_pinned) cudaFreeHost(w->h_pinned);
+  for (auto p : w->v64) cudaFree(p);
+  for (auto p : w->v32) cudaFree(p);
+  cudaFree(w->r64); cudaFree(w->xc); cudaFree(w->xd);
+  cudaFree(w->part); cudaFree(w->sc); cudaFree(w->out); cudaFree(w->cols); cudaFree(w->ticket);
+  if (w->h_pin) cudaFreeHost(w->h_pin);
+  if (w->gexec) cudaGraphExecDestroy(w->gexec);
   delete w;
 }
 
 void cpm_free_solve(cpm_ctx *c) {
   free_work(c->solve);
-  free_work(c->solve_adj);
-  free_work(c->solve64);
-  free_work(c->solve_adj64);
   c->solve = nullptr;
-  c->solve_adj = nullptr;
-  c->solve64 = nullptr;
-  c->solve_adj64 = nullptr;
 }
 
-static cpm_status get_work(cpm_ctx *c, SolveWork *&w, int64_t N, int nrhs, int64_t ld, int elem) {
-  if (w && w->nrhs == nrhs && w->ld == ld && w->elem == elem) return CPM_OK;
+// Reserve the solve workspace for N x ld (FP64 vectors always; FP32 inner
+// vectors and the refinement buffers with `fp32`).  The only allocation of the
+// solve path; called from cpm_set_boundary and cpm_reserve.
+cpm_status cpm_reserve_solve(cpm_ctx *c, int64_t ld, bool fp32) {
+  const int64_t N = c->NS + c->NC;
+  SolveWork *w = c->solve;
+  if (w && w->N == N && w->ld >= ld && (w->has32 || !fp32)) return CPM_OK;
+  if (w) { ld = std::max(ld, w->ld); fp32 = fp32 || w->has32; }
   free_work(w);
+  c->solve = nullptr;
   w = new SolveWork;
-  w->owner = c;
-  w->nrhs = nrhs; w->ld = ld; w->elem = elem;
-  size_t vb = (size_t)N * (size_t)ld * (size_t)elem;
-  for (auto &p : w->vec) CPM_CUDA_TRY(cudaMalloc(&p, vb));
-  CPM_CUDA_TRY(cudaMalloc(&w->r64, (size_t)N * ld * sizeof(double)));
-  CPM_CUDA_TRY(cudaMalloc(&w->fs, (size_t)N * ld * sizeof(double)));
-  if (elem == (int)sizeof(float)) {
-    CPM_CUDA_TRY(cudaMalloc(&w->f32, (size_t)N * ld * sizeof(float)));
-    CPM_CUDA_TRY(cudaMalloc(&w->xd, (size_t)N * ld * sizeof(double)));
+  w->N = N; w->ld = ld; w->has32 = fp32;
+  const size_t n = (size_t)std::max<int64_t>(N, 1) * (size_t)ld;
+  cpm_status rc = CPM_OK;
+  auto al = [&](void **p, size_t bytes) {
+    if (rc == CPM_OK && cudaMalloc(p, bytes) != cudaSuccess) { (void)cudaGetLastError(); rc = CPM_ERR_OOM; }
+  };
+  for (auto &p : w->v64) al((void **)&p, n * sizeof(double));
+  al((void **)&w->r64, n * sizeof(double));
+  if (fp32) {
+    for (auto &p : w->v32) al((void **)&p, n * sizeof(float));
+    al((void **)&w->xc, n * sizeof(double));
+    al((void **)&w->xd, n * sizeof(double));
   }
-  CPM_CUDA_TRY(cudaMalloc(&w->part, sizeof(double) * RED_BLOCKS * 3 * nrhs));
-  CPM_CUDA_TRY(cudaMalloc(&w->dots, sizeof(double) * 3 * nrhs));
-  CPM_CUDA_TRY(cudaMalloc(&w->sc, sizeof(double) * NSC * nrhs));
-  CPM_CUDA_TRY(cudaMalloc(&w->d_cols, sizeof(double) * 4 * nrhs));
-  CPM_CUDA_TRY(cudaMallocHost(&w->h_pinned, sizeof(double) * (NSC + 3) * nrhs));
+  w->G = 2 * c->nsm;
+  // partials for up to 4 blocks per SM (the autotuner's widest choice)
+  al((void **)&w->part, sizeof(double) * (size_t)(4 * c->nsm) * NQMAX * ld);
+  al((void **)&w->sc, sizeof(double) * NSC * ld);
+  al((void **)&w->out, sizeof(double) * NQMAX * ld);
+  al((void **)&w->cols, sizeof(double) * 4 * ld);
+  al((void **)&w->ticket, sizeof(unsigned));
+  if (rc == CPM_OK && cudaMallocHost((void **)&w->h_pin, sizeof(double) * (NSC + NQMAX) * ld) != cudaSuccess) {
+    (void)cudaGetLastError();
+    rc = CPM_ERR_OOM;
+  }
+  if (rc == CPM_OK && cudaMemset(w->ticket, 0, sizeof(unsigned)) != cudaSuccess) rc = CPM_ERR_CUDA;
+  if (rc != CPM_OK) { free_work(w); return rc; }
+  c->solve = w;
   return CPM_OK;
 }
 
-template <typename T>
-static void dots(SolveWork *w, int nq, const T *a0, const T *b0, const T *a1, const T *b1, const T *a2, const T *b2,
-                 int64_t N, cudaStream_t st, int64_t NS = 0, double wpde = 1.0) {
-  dots_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a0, b0, a1, b1, a2, b2, nq, N, NS, wpde, w->nrhs, w->ld,
-                                                     w->part);
-  reduce_parts_kernel<<<1, 256, 0, st>>>(w->part, RED_BLOCKS, nq, w->nrhs, w->dots);
-  if (w->owner) cpm_count_launches(w->owner, 2);
-}
+namespace {
 
-// operator with a PDE-row scale: v = R A u (or R A^T u)
+// operator product with a PDE-row scale R and a PDE-entry scale C: v = R A C u
+// (or R A^T C u)
 template <typename T>
-using ApplyFn = cpm_status (*)(cpm_ctx *, double, double, double, const T *, T *, int, int64_t, cudaStream_t);
+using ApplyFn = cpm_status (*)(cpm_ctx *, double, double, double, double, const T *, T *, int, int64_t,
+                               cudaStream_t);
 
-// Krylov variant: right diagonal preconditioning (the paper's form, Sec. 5.4)
-// or left row scaling (scaled residual)
-struct KrylovForm {
-  double right;     // PDE-row value of the right preconditioner (1: none)
-  double rowscale;  // PDE-row scale applied to the operator and rhs (1: none)
-  double stall;     // iterations without halving the residual before giving up
-  float shadow_mix;  // perturbation of the shadow residual (0: rhat = r)
+template <typename T>
+struct Op {
+  ApplyFn<T> fn;
+  double m, n, rowscale, colscale;
+  cpm_status operator()(cpm_ctx *c, const T *u, T *v, int nrhs, int64_t ld, cudaStream_t st, bool plain_cols) const {
+    return fn(c, m, n, rowscale, plain_cols ? 1.0 : colscale, u, v, nrhs, ld, st);
+  }
 };
 
+template <typename T>
+struct Vecs { T *r, *rh, *p, *v, *s, *t; };
+
+Red red_of(SolveWork *w, int nrhs) { return Red{w->part, w->ticket, w->sc, w->out, w->cols, nrhs}; }
+
 // one BiCGSTAB iteration for all active columns (device only)
-template <typename T, typename TX = T>
-static cpm_status iteration(cpm_ctx *c, ApplyFn<T> apply, const KrylovForm &form, double m, double n, TX *x,
-                            SolveWork *w, double tol, int decide, cudaStream_t st) {
-  const int64_t N = c->NS + c->NC, NS = c->NS;
-  const int nrhs = w->nrhs;
-  const int64_t ld = w->ld;
-  T *r = (T *)w->vec[0], *rh = (T *)w->vec[1], *p = (T *)w->vec[2], *v = (T *)w->vec[3], *s = (T *)w->vec[4],
-    *t = (T *)w->vec[5], *ph = (T *)w->vec[6], *sh = (T *)w->vec[7];
-  const T dS = T(form.right);
-  // without a right preconditioner D p = p and D s = s: no copies
-  if (form.right == 1.0) {
-    ph = p;
-    sh = s;
-  }
-  const unsigned g = cpm_grid(N * nrhs, 256);
-  dots<T>(w, 2, rh, r, rh, rh, nullptr, nullptr, N, st);
-  scal_rho_kernel<<<1, 256, 0, st>>>(w->sc, w->dots, nrhs);
-  upd_p_kernel<T><<<g, 256, 0, st>>>(w->sc, N, NS, nrhs, ld, dS, form.shadow_mix, r, rh, p, v, ph);
-  cpm_status rc = apply(c, m, n, form.rowscale, ph, v, nrhs, ld, st);
+template <typename T, typename TX>
+cpm_status iteration(cpm_ctx *c, const Op<T> &op, TX *x, const Vecs<T> &V, SolveWork *w, int nrhs, int64_t ld,
+                     const Conv &cv, cudaStream_t st) {
+  const int64_t N = c->NS + c->NC;
+  const Red R = red_of(w, nrhs);
+  const unsigned G = (unsigned)w->G;
+  kp_kernel<T><<<G, KT, 0, st>>>(w->sc, cv.mix, N, nrhs, ld, V.r, V.rh, V.p, V.v);
+  cpm_status rc = op(c, V.p, V.v, nrhs, ld, st, false);
   if (rc) return rc;
-  dots<T>(w, 1, rh, v, nullptr, nullptr, nullptr, nullptr, N, st);
-  scal_alpha_kernel<<<1, 256, 0, st>>>(w->sc, w->dots, nrhs);
-  upd_s_kernel<T><<<g, 256, 0, st>>>(w->sc, N, NS, nrhs, ld, dS, r, v, s, sh);
-  rc = apply(c, m, n, form.rowscale, sh, t, nrhs, ld, st);
+  dot_kernel<T, 1><<<G, KT, 0, st>>>(R, cv, ST_ALPHA, N, ld, V.rh, V.v);
+  ks_kernel<T><<<G, KT, 0, st>>>(w->sc, N, nrhs, ld, V.r, V.v, V.s);
+  rc = op(c, V.s, V.t, nrhs, ld, st, false);
   if (rc) return rc;
-  dots<T>(w, 2, t, s, t, t, nullptr, nullptr, N, st);
-  scal_omega_kernel<<<1, 256, 0, st>>>(w->sc, w->dots, nrhs);
-  upd_xr_kernel<T, TX><<<g, 256, 0, st>>>(w->sc, N, nrhs, ld, x, r, ph, sh, s, t);
-  dots<T>(w, 1, r, r, nullptr, nullptr, nullptr, nullptr, N, st);
-  scal_conv_kernel<<<1, 256, 0, st>>>(w->sc, w->dots, nrhs, tol, form.stall, decide);
-  cpm_count_launches(c, 7);  // 4 scalar + 3 vector kernels (products and dots count themselves)
+  dot_kernel<T, 2><<<G, KT, 0, st>>>(R, cv, ST_OMEGA, N, ld, V.t, V.s);
+  kxr_kernel<T, TX><<<G, KT, 0, st>>>(R, cv, N, c->NS, T(op.colscale), ld, x, V.r, V.rh, V.p, V.s, V.t);
+  cpm_count_launches(c, 5);
   return CPM_OK;
 }
 
-static cpm_status read_scalars(SolveWork *w, cudaStream_t st) {
-  CPM_CUDA_TRY(cudaMemcpyAsync(w->h_pinned, w->sc, sizeof(double) * NSC * w->nrhs, cudaMemcpyDeviceToHost, st));
+cpm_status read_scalars(SolveWork *w, int nrhs, cudaStream_t st) {
+  CPM_CUDA_TRY(cudaMemcpyAsync(w->h_pin, w->sc, sizeof(double) * NSC * nrhs, cudaMemcpyDeviceToHost, st));
   CPM_CUDA_TRY(cudaStreamSynchronize(st));
   return CPM_OK;
 }
 
-// BiCGSTAB on A x = f in one precision T; x holds the initial guess.
-// (x of a wider type TX than T requires x = 0 on entry: the initial product
-// is skipped)
-template <typename T, typename TX = T>
-static cpm_status bicgstab(cpm_ctx *c, ApplyFn<T> apply, const KrylovForm &form, double m, double n, const T *f,
-                           TX *x, SolveWork *w, double tol, int maxit, int check_every, int *iters, int *restarts,
-                           bool *broke, cudaStream_t st) {
-  const int64_t N = c->NS + c->NC;
-  const int nrhs = w->nrhs;
-  const int64_t ld = w->ld;
-  T *r = (T *)w->vec[0], *rh = (T *)w->vec[1], *p = (T *)w->vec[2], *v = (T *)w->vec[3];
-  const unsigned g = cpm_grid(N * nrhs, 256);
-  cpm_status rc = CPM_OK;
-  if constexpr (std::is_same<T, TX>::value) {
-    rc = apply(c, m, n, form.rowscale, x, r, nrhs, ld, st);
-    if (rc) return rc;
-  } else {
-    CPM_CUDA_TRY(cudaMemsetAsync(r, 0, sizeof(T) * (size_t)N * ld, st));
+// `steps` iterations: replayed from a cached graph when the group is a full
+// one and nothing is being profiled, launched directly otherwise
+template <typename T, typename TX>
+cpm_status iterations(cpm_ctx *c, const Op<T> &op, TX *x, const Vecs<T> &V, SolveWork *w, int nrhs, int64_t ld,
+                      const Conv &cv, int steps, bool graph, cudaStream_t st) {
+  if (graph && w->graphs_ok && !c->prof.on) {
+    GraphKey k;
+    std::memset(&k, 0, sizeof(k));
+    k.fn = (const void *)op.fn; k.m = op.m; k.n = op.n; k.rs = op.rowscale; k.cs = op.colscale;
+    k.tol = cv.tol; k.stall = cv.stall; k.mix = cv.mix; k.x = x; k.vecs = V.r; k.nrhs = nrhs; k.steps = steps;
+    k.elem = (int)sizeof(T); k.xelem = (int)sizeof(TX); k.ld = ld; k.G = w->G;
+    if (!(w->gexec && w->gkey == k)) {
+      if (w->gexec) { cudaGraphExecDestroy(w->gexec); w->gexec = nullptr; }
+      const int64_t before = c->prof.launches;
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      cpm_status rc = CPM_OK;
+      if (e == cudaSuccess) {
+        for (int s = 0; s < steps && rc == CPM_OK; ++s) rc = iteration<T, TX>(c, op, x, V, w, nrhs, ld, cv, st);
+        e = cudaStreamEndCapture(st, &g);
+      }
+      if (rc == CPM_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&w->gexec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      w->glaunches = c->prof.launches - before;
+      c->prof.launches = before;
+      if (rc != CPM_OK || e != cudaSuccess) {
+        // capture not available here: plain launches from now on
+        (void)cudaGetLastError();
+        if (w->gexec) { cudaGraphExecDestroy(w->gexec); w->gexec = nullptr; }
+        w->graphs_ok = false;
+        if (rc != CPM_OK) return rc;
+        return iterations<T, TX>(c, op, x, V, w, nrhs, ld, cv, steps, false, st);
+      }
+      w->gkey = k;
+    }
+    CPM_CUDA_TRY(cudaGraphLaunch(w->gexec, st));
+    cpm_count_launches(c, (int)w->glaunches);
+    return CPM_OK;
   }
-  init_r_kernel<T><<<g, 256, 0, st>>>(N, nrhs, ld, f, r, rh, p, v);
-  cpm_count_launches(c, 1);
-  dots<T>(w, 2, r, r, f, f, nullptr, nullptr, N, st);
-  scal_init_kernel<<<1, 256, 0, st>>>(w->sc, w->dots, nrhs, tol);
-  cpm_count_launches(c, 1);
+  for (int s = 0; s < steps; ++s) {
+    cpm_status rc = iteration<T, TX>(c, op, x, V, w, nrhs, ld, cv, st);
+    if (rc) return rc;
+  }
+  CPM_CUDA_TRY(cudaGetLastError());
+  return CPM_OK;
+}
+
+// BiCGSTAB iterations for all active columns until none is active or maxit:
+// the host reads the per-column flags every check_every iterations
+template <typename T, typename TX>
+cpm_status krylov_run(cpm_ctx *c, const Op<T> &op, TX *x, const Vecs<T> &V, SolveWork *w, int nrhs, int64_t ld,
+                      const Conv &cv, int maxit, int check_every, int *iters, int *restarts, bool *broke,
+                      cudaStream_t st) {
   int it = 0;
-  *broke = false;
+  const bool graph = std::getenv("CPM_NO_GRAPHS") == nullptr;
+  const bool trace = std::getenv("CPM_SOLVE_TRACE") != nullptr;
   while (true) {
-    rc = read_scalars(w, st);
+    cpm_status rc = read_scalars(w, nrhs, st);
     if (rc) return rc;
     bool any = false;
-    int nrestart = 0;
+    int nrestart = 0, nact = 0, nbroke = 0, nstop = 0;
+    double worst = 0.0;
     for (int q = 0; q < nrhs; ++q) {
-      const double *sq = w->h_pinned + q * NSC;
-      if (sq[5] != 0.0) any = true;
-      if (sq[10] != 0.0) *broke = true;
-      nrestart += (int)sq[7];
+      const double *sq = w->h_pin + q * NSC;
+      if (sq[S_ACTIVE] != 0.0) { any = true; ++nact; }
+      if (sq[S_BROKE] != 0.0) { *broke = true; ++nbroke; }
+      if (sq[S_STOPPED] != 0.0) ++nstop;
+      nrestart += (int)sq[S_NRESTART];
+      worst = std::max(worst, std::sqrt(sq[S_RN2] / sq[S_FN2]));
     }
     *restarts = nrestart;
+    if (trace)
+      std::fprintf(stderr, "[cpm it] %d recursive relres[0] %.3e worst %.3e active %d broke %d stopped %d restarts %d\n",
+                   it, std::sqrt(w->h_pin[S_RN2] / w->h_pin[S_FN2]), worst, nact, nbroke, nstop, nrestart);
     if (!any || it >= maxit) break;
-    int steps = std::min(check_every, maxit - it);
-    for (int k = 0; k < steps; ++k) {
-      rc = iteration<T, TX>(c, apply, form, m, n, x, w, tol, 1, st);
-      if (rc) return rc;
-    }
-    CPM_CUDA_TRY(cudaGetLastError());
+    const int steps = std::min(check_every, maxit - it);
+    rc = iterations<T, TX>(c, op, x, V, w, nrhs, ld, cv, steps, graph && steps == check_every, st);
+    if (rc) return rc;
     it += steps;
   }
   *iters = it;
   return CPM_OK;
 }
 
+// BiCGSTAB on the iterated system (op) with right-hand side f; x holds the
+// initial guess (x_zero: x = 0, which a wider accumulator TX requires)
+template <typename T, typename TX>
+cpm_status bicgstab(cpm_ctx *c, const Op<T> &op, const T *f, TX *x, bool x_zero, const Vecs<T> &V, SolveWork *w,
+                    int nrhs, int64_t ld, const Conv &cv, int maxit, int check_every, int *iters, int *restarts,
+                    bool *broke, cudaStream_t st) {
+  const int64_t N = c->NS + c->NC;
+  const Red R = red_of(w, nrhs);
+  cpm_status rc = CPM_OK;
+  if (!x_zero) {
+    if constexpr (std::is_same<T, TX>::value) {
+      rc = op(c, x, V.r, nrhs, ld, st, true);  // r = R A x (x in the original variables)
+      if (rc) return rc;
+    } else {
+      return CPM_ERR_ARG;
+    }
+  }
+  init_kernel<T><<<(unsigned)w->G, KT, 0, st>>>(R, cv, N, ld, x_zero, f, V.r, V.rh, V.p, V.v);
+  cpm_count_launches(c, 1);
+  *broke = false;
+  return krylov_run<T, TX>(c, op, x, V, w, nrhs, ld, cv, maxit, check_every, iters, restarts, broke, st);
+}
+
 // FP64 residual r64 = f - A x and its squared weighted norms per column:
 // |W r|^2 and |W f|^2 with W = diag(wrow on PDE rows, 1 on BC rows)
-static cpm_status residual64(cpm_ctx *c, ApplyFn<double> apply, double m, double n, const double *f, const double *x,
-                             SolveWork *w, double wrow, std::vector<double> &rn2, std::vector<double> &fn2,
-                             cudaStream_t st) {
+cpm_status residual64(cpm_ctx *c, ApplyFn<double> fn, double m, double n, const double *f, const double *x,
+                      SolveWork *w, int nrhs, int64_t ld, double wrow, std::vector<double> &rn2,
+                      std::vector<double> &fn2, cudaStream_t st) {
   const int64_t N = c->NS + c->NC;
-  cpm_status rc = apply(c, m, n, 1.0, x, w->r64, w->nrhs, w->ld, st);
+  cpm_status rc = fn(c, m, n, 1.0, 1.0, x, w->r64, nrhs, ld, st);
   if (rc) return rc;
-  residual64_kernel<<<cpm_grid(N * w->nrhs, 256), 256, 0, st>>>(N, w->nrhs, w->ld, f, w->r64);
+  resid_kernel<<<(unsigned)w->G, KT, 0, st>>>(red_of(w, nrhs), N, c->NS, wrow * wrow, ld, f, w->r64);
   cpm_count_launches(c, 1);
-  dots<double>(w, 2, w->r64, w->r64, f, f, nullptr, nullptr, N, st, c->NS, wrow * wrow);
-  CPM_CUDA_TRY(cudaMemcpyAsync(w->h_pinned, w->dots, sizeof(double) * 2 * w->nrhs, cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaMemcpyAsync(w->h_pin, w->out, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
   CPM_CUDA_TRY(cudaStreamSynchronize(st));
-  rn2.assign(w->h_pinned, w->h_pinned + w->nrhs);
-  fn2.assign(w->h_pinned + w->nrhs, w->h_pinned + 2 * w->nrhs);
+  rn2.assign(w->h_pin, w->h_pin + nrhs);
+  fn2.assign(w->h_pin + nrhs, w->h_pin + 2 * nrhs);
   return CPM_OK;
 }
 
-static double relres_of(double rn2, double fn2) {
+double relres_of(double rn2, double fn2) {
   double fnq = fn2 > 0 ? std::sqrt(fn2) : 1.0;
   double rr = std::sqrt(rn2) / fnq;
   return std::isfinite(rr) ? rr : INFINITY;
 }
 
-static double worst_relres(const std::vector<double> &rn2, const std::vector<double> &fn2) {
+// The FP64 rounding floor of the true residual: storing the exact solution in
+// FP64 perturbs each entry by up to half an ulp, and the operator amplifies
+// that noise by about its row norm (O(1/h^2) on PDE rows), so the relative
+// residual of any FP64 x cannot fall much below
+//   floor = (u / sqrt 3) |W A (x o xi)|_2 / |W f|_2,   u = 2^-53,
+// with xi a fixed random +-1 vector (the rounding model: independent relative
+// errors of variance u^2 / 3).  A column converges when its true relative
+// residual is at most max(tol, 4 floor).  Needs two [N][ld] FP64 scratch vectors.
+cpm_status floor64(cpm_ctx *c, ApplyFn<double> fn, double m, double n, const double *x, double *y, double *Ay,
+                   SolveWork *w, int nrhs, int64_t ld, double wrow, const std::vector<double> &fn2,
+                   std::vector<double> &floors, cudaStream_t st) {
+  const int64_t N = c->NS + c->NC;
+  sign_perturb_kernel<<<cpm_grid(N * nrhs, 256), 256, 0, st>>>(N, nrhs, ld, x, y);
+  cpm_status rc = fn(c, m, n, 1.0, 1.0, y, Ay, nrhs, ld, st);
+  if (rc) return rc;
+  wnorm_kernel<<<(unsigned)w->G, KT, 0, st>>>(red_of(w, nrhs), N, c->NS, wrow * wrow, ld, Ay);
+  cpm_count_launches(c, 2);
+  CPM_CUDA_TRY(cudaMemcpyAsync(w->h_pin, w->out, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaStreamSynchronize(st));
+  const double u = std::ldexp(1.0, -53);
+  floors.resize(nrhs);
+  for (int q = 0; q < nrhs; ++q) floors[q] = (u / std::sqrt(3.0)) * relres_of(w->h_pin[q], fn2[q]);
+  return CPM_OK;
+}
+
+// converged: within tol, or within four times the rounding floor
+bool done_col(double rn2, double fn2, double tol, double floor_q) {
+  const double r = relres_of(rn2, fn2);
+  return r <= tol || r <= 4.0 * floor_q;
+}
+
+double worst_relres(const std::vector<double> &rn2, const std::vector<double> &fn2) {
   double worst = 0.0;
   for (size_t q = 0; q < rn2.size(); ++q) worst = std::max(worst, relres_of(rn2[q], fn2[q]));
   return worst;
 }
 
-// Mixed-precision iterative refinement with restarted inner solves: each
-// outer step takes the FP64 residual r = f - A x, solves (W A) d = W r / |W r|
-// by FP32 BiCGSTAB from d = 0 to the relative inner tolerance, and adds
-// |W r| d to x in FP64.  Every inner solve starts a fresh Krylov space, so a
-// loss of accuracy in one FP32 solve does not carry into the next.  A column
-// whose FP64 residual fails to halve over two outer steps is left for the
-// FP64 finish.  rhs_w weights the PDE rows of the inner right-hand side: the
-// scaling of the left-scaled form, or 1 for a right-preconditioned inner form.
-static cpm_status ir_restarted(cpm_ctx *c, ApplyFn<double> ap64, ApplyFn<float> ap32, const KrylovForm &form32,
-                               double m, double n, const double *f, double *x, SolveWork *w, double wrow,
-                               double rhs_w, double tol, double inner_tol, int inner_maxit, int maxit, int max_outer,
-                               int check_every, bool trace, int *iters, int *outers, int *restarts,
-                               std::vector<double> &rn2, std::vector<double> &fn2, cudaStream_t st) {
+// Mixed-precision iterative refinement by residual replacement ("reliable
+// updates"): one FP32 BiCGSTAB runs on the correction equation (the iterated
+// form of A d = r), its updates accumulated straight into the FP64 solution x.
+// Whenever a column's recursive FP32 residual has dropped by `delta` relative
+// to its last replacement, the host computes the FP64 residual r = f - A x
+// (difference-form product, accurate to the FP64 rounding of local
+// differences), stops the columns that meet tol there, and replaces the FP32
+// residual of the others by r (scaled as the iterated form needs), keeping the
+// search direction p and the shadow residual: the Krylov space survives the
+// refinement step, unlike a restarted inner solve, so the FP32 iteration count
+// stays close to an FP64 solve's.  Each replacement bounds the gap between the
+// recursive and the true residual, which the FP32 operator's rounding (about
+// eps_32 times the stencil's local amplification) otherwise lets grow.  A
+// column whose FP64 residual fails to fall over three replacements is left for
+// the FP64 finish.  rhs_w weights the PDE rows of the FP32 residual: the
+// scaling of the left-scaled form, or 1 for a right-preconditioned form.
+cpm_status ir_reliable(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, double m, double n,
+                       const double *f, double *x, SolveWork *w, int nrhs, int64_t ld, double wrow, double rhs_w,
+                       double tol, double delta, int maxit, int max_repl, int check_every, bool trace, int *iters,
+                       int *nrepl_out, int *restarts, std::vector<double> &rn2, std::vector<double> &fn2,
+                       std::vector<double> &floors, cudaStream_t st) {
   const int64_t N = c->NS + c->NC;
-  const int nrhs = w->nrhs;
-  const int64_t ld = w->ld;
   const unsigned g = cpm_grid(N * nrhs, 256);
-  double *d_scale = w->d_cols;
-  std::vector<double> scale(nrhs, 0.0), best(nrhs, INFINITY);
+  Vecs<float> V{w->v32[0], w->v32[1], w->v32[2], w->v32[3], w->v32[4], w->v32[5]};
+  float *f32 = w->v32[5];  // first right-hand side: read by the init kernel before t is written
+  const Conv cv{delta, 4000.0, 0.5f};
+  const Red R = red_of(w, nrhs);
+  std::vector<double> flag(nrhs, 0.0), best(nrhs, INFINITY);
   std::vector<int> stall(nrhs, 0);
-  std::vector<char> act(nrhs, 1);
-  cpm_status rc = residual64(c, ap64, m, n, f, x, w, wrow, rn2, fn2, st);
+  floors.assign(nrhs, 0.0);
+  cpm_status rc = residual64(c, ap64, m, n, f, x, w, nrhs, ld, wrow, rn2, fn2, st);
   if (rc) return rc;
-  int it_total = 0, nout = 0, nrs = 0;
-  while (nout < max_outer && it_total < maxit) {
+  int it_total = 0, nrep = 0, nrs = 0;
+  bool first = true;
+  while (true) {
+    // the rounding floor matters once the residual nears the tolerance
+    if (worst_relres(rn2, fn2) > tol && worst_relres(rn2, fn2) < 1e3 * tol) {
+      rc = floor64(c, ap64, m, n, x, w->xc, w->v64[0], w, nrhs, ld, wrow, fn2, floors, st);
+      if (rc) return rc;
+    }
     bool any = false;
     for (int q = 0; q < nrhs; ++q) {
-      if (!act[q]) { scale[q] = 0.0; continue; }
-      if (relres_of(rn2[q], fn2[q]) <= tol) { act[q] = 0; scale[q] = 0.0; continue; }
+      flag[q] = 0.0;
+      if (done_col(rn2[q], fn2[q], tol, floors[q])) continue;
       if (rn2[q] < 0.25 * best[q]) { best[q] = rn2[q]; stall[q] = 0; }
-      else if (++stall[q] >= 2) { act[q] = 0; scale[q] = 0.0; continue; }
-      scale[q] = std::sqrt(rn2[q]);
+      else if (++stall[q] >= 3) continue;  // no gain over three replacements: FP64 finish
+      flag[q] = 1.0;
       any = true;
     }
     if (trace)
-      std::fprintf(stderr, "[cpm ir] outer %d it %d relres[0] %.3e worst %.3e\n", nout, it_total,
+      std::fprintf(stderr, "[cpm ru] replacement %d it %d relres[0] %.3e worst %.3e\n", nrep, it_total,
                    relres_of(rn2[0], fn2[0]), worst_relres(rn2, fn2));
-    if (!any) break;
-    CPM_CUDA_TRY(cudaMemcpyAsync(d_scale, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-    ir_rhs_kernel<<<g, 256, 0, st>>>(N, c->NS, rhs_w, nrhs, ld, d_scale, w->r64, w->f32);
-    CPM_CUDA_TRY(cudaMemsetAsync(w->xd, 0, sizeof(double) * (size_t)N * ld, st));
-    cpm_count_launches(c, 1);
+    if (!any || it_total >= maxit || nrep >= max_repl) break;
+    CPM_CUDA_TRY(cudaMemcpyAsync(w->cols, flag.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+    if (first) {
+      // r = W r64 on the selected columns (0 elsewhere), rhat = r, p = v = 0
+      ir_rhs_kernel<<<g, 256, 0, st>>>(N, c->NS, rhs_w, nrhs, ld, w->cols, w->r64, f32);
+      init_kernel<float><<<(unsigned)w->G, KT, 0, st>>>(R, cv, N, ld, true, f32, V.r, V.rh, V.p, V.v);
+      cpm_count_launches(c, 2);
+      first = false;
+    } else {
+      repl_kernel<float><<<(unsigned)w->G, KT, 0, st>>>(R, cv, N, c->NS, rhs_w, ld, w->r64, V.r, V.rh);
+      cpm_count_launches(c, 1);
+    }
+    ++nrep;
     int it = 0, rs = 0;
     bool broke = false;
-    rc = bicgstab<float, double>(c, ap32, form32, m, n, w->f32, w->xd, w, inner_tol,
-                                 std::min(inner_maxit, maxit - it_total), check_every, &it, &rs, &broke, st);
+    rc = krylov_run<float, double>(c, op32, x, V, w, nrhs, ld, cv, maxit - it_total, check_every, &it, &rs, &broke,
+                                   st);
     if (rc) return rc;
     it_total += it;
-    nrs += rs;
-    // keep the correction only where the FP64 residual went down; a column
-    // whose FP32 solve made it worse is left for the FP64 finish
-    ir_candidate_kernel<<<g, 256, 0, st>>>(N, nrhs, ld, d_scale, w->xd, x, w->fs);
-    cpm_count_launches(c, 1);
-    ++nout;
-    std::vector<double> rn2_prev = rn2;
-    rc = residual64(c, ap64, m, n, f, w->fs, w, wrow, rn2, fn2, st);
+    nrs = rs;
+    rc = residual64(c, ap64, m, n, f, x, w, nrhs, ld, wrow, rn2, fn2, st);
     if (rc) return rc;
-    std::vector<double> acc(nrhs, 0.0);
-    bool rejected = false;
-    for (int q = 0; q < nrhs; ++q) {
-      if (scale[q] == 0.0) { rn2[q] = rn2_prev[q]; continue; }
-      if (std::isfinite(rn2[q]) && rn2[q] < rn2_prev[q]) {
-        acc[q] = 1.0;
-      } else {
-        rejected = true;
-        act[q] = 0;
-        rn2[q] = rn2_prev[q];
-      }
-    }
-    CPM_CUDA_TRY(cudaMemcpyAsync(d_scale, acc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-    accept_kernel<<<g, 256, 0, st>>>(N, nrhs, ld, d_scale, w->fs, x);
-    cpm_count_launches(c, 1);
-    if (rejected) {
-      // r64 must hold the residual of x for the next outer step
-      rc = residual64(c, ap64, m, n, f, x, w, wrow, rn2, fn2, st);
-      if (rc) return rc;
-    }
   }
   *iters = it_total;
-  *outers = nout;
+  *nrepl_out = nrep;
   *restarts = nrs;
   return CPM_OK;
 }
 
-static cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const double *f, double *x, int nrhs,
-                             int64_t ld, const cpm_solve_opts *o, cpm_solve_stats *stats, cudaStream_t st) {
-  cpm_solve_opts opts{1e-10, 10000, CPM_SOLVE_FP64, 1e-2, 200, 16, CPM_NORM_SCALED, 1000};
+// FP64 BiCGSTAB passes from the current x: the recursively updated residual
+// drifts from f - A x near the rounding level, so while the true residual is
+// above tol the iteration restarts from the current x, as long as a pass still
+// halves the worst true residual
+cpm_status fp64_passes(cpm_ctx *c, ApplyFn<double> ap64, bool left, double dS, double m, double n, const double *f,
+                       double *x, SolveWork *w, int nrhs, int64_t ld, double wrow, double tol, int maxit,
+                       int check_every, int *iters, int *restarts, bool *broke, std::vector<double> &rn2,
+                       std::vector<double> &fn2, std::vector<double> &floors, cudaStream_t st) {
+  const int64_t N = c->NS + c->NC;
+  Vecs<double> V{w->v64[0], w->v64[1], w->v64[2], w->v64[3], w->v64[4], w->v64[5]};
+  const Op<double> op = left ? Op<double>{ap64, m, n, dS, 1.0} : Op<double>{ap64, m, n, 1.0, dS};
+  const Conv cv{tol, 4000.0, 0.0f};
+  double prev_worst = INFINITY;
+  for (int pass = 0; pass < 6; ++pass) {
+    const double *rhs = f;
+    if (left) {
+      // W f into the t slot, which the initial residual reads before t is written
+      scale_rows64_kernel<<<cpm_grid(N * nrhs, 256), 256, 0, st>>>(N, c->NS, nrhs, ld, dS, f, V.t);
+      cpm_count_launches(c, 1);
+      rhs = V.t;
+    }
+    int it = 0, rs = 0;
+    cpm_status rc = bicgstab<double, double>(c, op, rhs, x, false, V, w, nrhs, ld, cv, maxit - *iters, check_every,
+                                             &it, &rs, broke, st);
+    if (rc) return rc;
+    *iters += it;
+    *restarts += rs;
+    rc = residual64(c, ap64, m, n, f, x, w, nrhs, ld, wrow, rn2, fn2, st);
+    if (rc) return rc;
+    const double worst = worst_relres(rn2, fn2);
+    if (worst > tol) {
+      // t and s are free between passes
+      rc = floor64(c, ap64, m, n, x, V.t, V.s, w, nrhs, ld, wrow, fn2, floors, st);
+      if (rc) return rc;
+    }
+    bool all = true;
+    for (int q = 0; q < nrhs; ++q) all = all && done_col(rn2[q], fn2[q], tol, floors[q]);
+    if (all || *broke || *iters >= maxit || !(worst < 0.5 * prev_worst)) break;
+    prev_worst = worst;
+  }
+  return CPM_OK;
+}
+
+cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const double *f, double *x, int nrhs,
+                      int64_t ld, const cpm_solve_opts *o, cpm_solve_stats *stats, cudaStream_t st) {
+  cpm_solve_opts opts{1e-10, 10000, CPM_SOLVE_FP64, 1e-2, 200, 16, CPM_NORM_PLAIN, 1000};
   if (o) opts = *o;
   if (opts.tol <= 0) opts.tol = 1e-10;
   if (opts.maxit <= 0) opts.maxit = 10000;
@@ -595,97 +1002,83 @@ static cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const
   if (opts.max_refine <= 0) opts.max_refine = 200;
   if (opts.check_every <= 0) opts.check_every = 16;
   if (opts.inner_maxit <= 0) opts.inner_maxit = 1000;
-  if (opts.norm != CPM_NORM_PLAIN) opts.norm = CPM_NORM_SCALED;
+  if (opts.norm != CPM_NORM_SCALED) opts.norm = CPM_NORM_PLAIN;
   const bool scaled = (opts.norm == CPM_NORM_SCALED);
   const bool trace = std::getenv("CPM_SOLVE_TRACE") != nullptr;
+  SolveWork *w = c->solve;
   const int64_t N = c->NS + c->NC;
+  if (!w || w->N != N || ld > w->ld) return CPM_ERR_CAPACITY;
+  if (opts.mode == CPM_SOLVE_FP32_IR && !w->has32) return CPM_ERR_CAPACITY;
   // Jacobi value of the PDE rows: 1/(m + n diag L) (Sec. 5.4)
   const double dS = 1.0 / (m + n * (-2.0 * c->dim / (c->h * c->h)));
   // residual weight of the PDE rows; the adjoint (iterated right-preconditioned,
   // see below) is measured on its unscaled residual, the iteration's own
   const double wrow = (scaled && !adjoint) ? dS : 1.0;
-  SolveWork *&w = adjoint ? c->solve_adj : c->solve;
   cpm_status rc;
   int iters = 0, restarts = 0, refinements = 0, iters64 = 0;
   bool broke = false;
-  std::vector<double> rn2, fn2;
-  ApplyFn<double> ap64 = adjoint ? cpm_apply_transpose_scaled_T<double> : cpm_apply_scaled_T<double>;
+  std::vector<double> rn2, fn2, floors(nrhs, 0.0);
+  ApplyFn<double> ap64 = adjoint ? cpm_apply_transpose_rc_T<double> : cpm_apply_rc_T<double>;
   // scaled: BiCGSTAB on (W A) x = W f, so its recursive residual is the
   // measured one; plain: the paper's right-preconditioned form.  The adjoint
   // always iterates right-preconditioned, A^T W mu = g with lambda = W mu: this
   // is the transpose of the row-scaled forward system, whereas scaling the rows
   // of A^T leaves the BC rows with O(1/h^2) couplings and BiCGSTAB breaks down.
   const bool left = scaled && !adjoint;
-  KrylovForm form = left ? KrylovForm{1.0, dS, 4000.0, 0.0f} : KrylovForm{dS, 1.0, 4000.0, 0.0f};
-  if (opts.mode == CPM_SOLVE_FP64) {
-    rc = get_work(c, w, N, nrhs, ld, sizeof(double));
-    if (rc) return rc;
-    const double *rhs = f;
-    if (left) {
-      scale_rows64_kernel<<<cpm_grid(N * nrhs, 256), 256, 0, st>>>(N, c->NS, nrhs, ld, dS, f, w->fs);
-      cpm_count_launches(c, 1);
-      rhs = w->fs;
-    }
-    // the recursively updated residual drifts from f - A x near the rounding
-    // level; while the true residual is above tol, restart from the current x
-    double prev_worst = INFINITY;
-    for (int pass = 0; pass < 6; ++pass) {
-      int it = 0, rs = 0;
-      rc = bicgstab<double>(c, ap64, form, m, n, rhs, x, w, opts.tol, opts.maxit - iters, opts.check_every, &it, &rs,
-                            &broke, st);
-      if (rc) return rc;
-      iters += it;
-      iters64 += it;
-      restarts += rs;
-      rc = residual64(c, ap64, m, n, f, x, w, wrow, rn2, fn2, st);
-      if (rc) return rc;
-      double worst = worst_relres(rn2, fn2);
-      // stop at the attainable accuracy: a restart that does not halve the worst
-      // true residual gains nothing more
-      if (worst <= opts.tol || broke || iters >= opts.maxit || !(worst < 0.5 * prev_worst)) break;
-      prev_worst = worst;
-    }
-  } else if (opts.mode == CPM_SOLVE_FP32_IR) {
-    ApplyFn<float> ap32 = adjoint ? cpm_apply_transpose_scaled_T<float> : cpm_apply_scaled_T<float>;
-    // the FP32 iteration always runs on the row-scaled system (its residual is
-    // balanced); the requested norm decides acceptance and convergence
-    KrylovForm form32 = adjoint ? KrylovForm{dS, 1.0, 4000.0, 0.5f} : KrylovForm{1.0, dS, 4000.0, 0.5f};
-    rc = get_work(c, w, N, nrhs, ld, sizeof(float));
-    if (rc) return rc;
-    rc = ir_restarted(c, ap64, ap32, form32, m, n, f, x, w, wrow, adjoint ? 1.0 : dS, opts.tol, opts.inner_tol, opts.inner_maxit,
-                      opts.maxit, opts.max_refine, opts.check_every, trace, &iters, &refinements, &restarts, rn2, fn2,
-                      st);
-    if (rc) return rc;
-    if (!(worst_relres(rn2, fn2) <= opts.tol) && iters < opts.maxit) {
-      // FP64 finish from the current iterate for the columns the FP32 phase
-      // left above tol (columns already converged stay frozen)
-      if (trace) std::fprintf(stderr, "[cpm] FP64 finish from relres %.3e\n", worst_relres(rn2, fn2));
-      SolveWork *&w64 = adjoint ? c->solve_adj64 : c->solve64;
-      rc = get_work(c, w64, N, nrhs, ld, sizeof(double));
-      if (rc) return rc;
-      const double *rhs = f;
-      if (left) {
-        scale_rows64_kernel<<<cpm_grid(N * nrhs, 256), 256, 0, st>>>(N, c->NS, nrhs, ld, dS, f, w64->fs);
-        cpm_count_launches(c, 1);
-        rhs = w64->fs;
+  CPM_CUDA_TRY(cudaMemsetAsync(w->ticket, 0, sizeof(unsigned), st));
+  w->G = c->nsm * ((c->tune.vec_blocks_per_sm >= 1 && c->tune.vec_blocks_per_sm <= 4) ? c->tune.vec_blocks_per_sm : 2);
+  // the initial residual: a right-hand side (or guess) that is not finite is
+  // rejected before any iteration
+  rc = residual64(c, ap64, m, n, f, x, w, nrhs, ld, wrow, rn2, fn2, st);
+  if (rc) return rc;
+  for (int q = 0; q < nrhs; ++q)
+    if (!std::isfinite(fn2[q]) || !std::isfinite(rn2[q])) {
+      if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->relres = NAN;
+        stats->status = CPM_ERR_ARG;
       }
-      int it = 0, rs = 0;
-      broke = false;
-      rc = bicgstab<double>(c, ap64, form, m, n, rhs, x, w64, opts.tol, opts.maxit - iters, opts.check_every, &it,
-                            &rs, &broke, st);
+      return CPM_ERR_ARG;
+    }
+  if (opts.mode == CPM_SOLVE_FP64) {
+    rc = fp64_passes(c, ap64, left, dS, m, n, f, x, w, nrhs, ld, wrow, opts.tol, opts.maxit, opts.check_every, &iters,
+                     &restarts, &broke, rn2, fn2, floors, st);
+    if (rc) return rc;
+    iters64 = iters;
+  } else if (opts.mode == CPM_SOLVE_FP32_IR) {
+    ApplyFn<float> ap32 = adjoint ? cpm_apply_transpose_rc_T<float> : cpm_apply_rc_T<float>;
+    // the FP32 iteration runs on the row-scaled system (its residual is
+    // balanced), the adjoint right-preconditioned; the requested norm decides
+    // acceptance and convergence
+    const Op<float> op32 = adjoint ? Op<float>{ap32, m, n, 1.0, dS} : Op<float>{ap32, m, n, dS, 1.0};
+    rc = ir_reliable(c, ap64, op32, m, n, f, x, w, nrhs, ld, wrow, adjoint ? 1.0 : dS, opts.tol, opts.inner_tol,
+                     opts.maxit, opts.max_refine, opts.check_every, trace, &iters, &refinements, &restarts, rn2, fn2,
+                     floors, st);
+    if (rc) return rc;
+    bool all = true;
+    for (int q = 0; q < nrhs; ++q) all = all && done_col(rn2[q], fn2[q], opts.tol, floors[q]);
+    if (!all && iters < opts.maxit) {
+      // FP64 finish from the current iterate for the columns the FP32 phase
+      // left above tol
+      if (trace) std::fprintf(stderr, "[cpm] FP64 finish from relres %.3e\n", worst_relres(rn2, fn2));
+      int it64 = 0;
+      rc = fp64_passes(c, ap64, left, dS, m, n, f, x, w, nrhs, ld, wrow, opts.tol, opts.maxit - iters,
+                       opts.check_every, &it64, &restarts, &broke, rn2, fn2, floors, st);
       if (rc) return rc;
-      iters += it;
-      iters64 += it;
-      restarts += rs;
-      rc = residual64(c, ap64, m, n, f, x, w64, wrow, rn2, fn2, st);
-      if (rc) return rc;
+      iters += it64;
+      iters64 += it64;
     }
   } else {
     return CPM_ERR_ARG;
   }
-  double relres = worst_relres(rn2, fn2);
+  double relres = worst_relres(rn2, fn2), floor_max = 0.0;
+  bool conv = true;
+  for (int q = 0; q < nrhs; ++q) {
+    conv = conv && done_col(rn2[q], fn2[q], opts.tol, floors[q]);
+    floor_max = std::max(floor_max, floors[q]);
+  }
   cpm_status out = CPM_OK;
-  if (!(relres <= opts.tol)) out = broke ? CPM_ERR_BREAKDOWN : CPM_ERR_NOT_CONVERGED;
+  if (!conv) out = broke ? CPM_ERR_BREAKDOWN : CPM_ERR_NOT_CONVERGED;
   if (stats) {
     stats->iterations = iters;
     stats->refinements = refinements;
@@ -693,11 +1086,72 @@ static cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const
     stats->relres = relres;
     stats->status = out;
     stats->fp64_iterations = iters64;
+    stats->relres_floor = floor_max;
   }
   return out;
 }
 
+}  // namespace
+
 cpm_status cpm_internal_solve(cpm_ctx *c, bool adjoint, double m, double n, const double *f, double *x, int nrhs,
-                              int64_t ld, const cpm_solve_opts *o, cpm_solve_stats *stats, cudaStream_t st) {
-  return solve_impl(c, adjoint, m, n, f, x, nrhs, ld, o, stats, st);
+                              int64_t ld, const cpm_solve_opts *o, cpm_solve_stats *stats, cudaStream_t caller) {
+  // run on the internal stream, ordered after the caller's prior work and
+  // before its later work
+  cudaStream_t st = c->istream ? c->istream : caller;
+  if (st != caller) {
+    CPM_CUDA_TRY(cudaEventRecord(c->ev_join[0], caller));
+    CPM_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_join[0], 0));
+  }
+  cpm_status rc = solve_impl(c, adjoint, m, n, f, x, nrhs, ld, o, stats, st);
+  if (st != caller) {
+    cudaError_t e1 = cudaEventRecord(c->ev_join[1], st);
+    cudaError_t e2 = cudaStreamWaitEvent(caller, c->ev_join[1], 0);
+    if (rc == CPM_OK && (e1 != cudaSuccess || e2 != cudaSuccess)) rc = cpm_internal_cuda_err(e1 ? e1 : e2);
+  }
+  return rc;
 }
+
+// Timing of the Krylov vector kernels for the autotuner: `reps` launches of the
+// two-product dot kernel over the workspace's first two vectors of precision
+// prec with G blocks (no scalar state is touched).  Returns milliseconds per
+// launch.
+cpm_status cpm_time_vector_kernels(cpm_ctx *c, int prec, int nrhs, int64_t ld, int G, int reps, cudaStream_t st,
+                                   double *ms) {
+  SolveWork *w = c->solve;
+  if (!w || ld > w->ld || (prec == CPM_PREC_FP32 && !w->has32) || G < 1 || G > 4 * c->nsm) return CPM_ERR_CAPACITY;
+  const int64_t N = c->NS + c->NC;
+  Red R = red_of(w, nrhs);
+  const Conv cv{0.0, 0.0, 0.0f};
+  cudaEvent_t e0, e1;
+  CPM_CUDA_TRY(cudaEventCreate(&e0));
+  CPM_CUDA_TRY(cudaEventCreate(&e1));
+  CPM_CUDA_TRY(cudaMemsetAsync(w->ticket, 0, sizeof(unsigned), st));
+  auto launch = [&]() {
+    if (prec == CPM_PREC_FP32)
+      dot_kernel<float, 2><<<(unsigned)G, KT, 0, st>>>(R, cv, ST_OUT, N, ld, w->v32[0], w->v32[1]);
+    else
+      dot_kernel<double, 2><<<(unsigned)G, KT, 0, st>>>(R, cv, ST_OUT, N, ld, w->v64[0], w->v64[1]);
+  };
+  R.sc = nullptr;  // the dot bodies then include every column
+  launch();
+  cudaEventRecord(e0, st);
+  for (int k = 0; k < reps; ++k) launch();
+  cudaEventRecord(e1, st);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cpm_internal_cuda_err(e);
+  *ms = (double)t / reps;
+  return CPM_OK;
+}
+
+cpm_status cpm_solve_buffers_of(cpm_ctx *c, int prec, cpm_solve_buffers *b) {
+  SolveWork *w = c->solve;
+  if (!w || (prec == CPM_PREC_FP32 && !w->has32)) return CPM_ERR_CAPACITY;
+  if (prec == CPM_PREC_FP32) { b->u = w->v32[0]; b->v = w->v32[1]; }
+  else { b->u = w->v64[0]; b->v = w->v64[1]; }
+  return CPM_OK;
+}
+

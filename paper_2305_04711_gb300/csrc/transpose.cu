@@ -33,12 +33,13 @@ __device__ __forceinline__ int64_t loc_of(const BandView &v, int32_t b, int lx, 
   return ((int64_t)b << 9) | (int64_t)((lz & 7) * 64 + (ly & 7) * 8 + (lx & 7));
 }
 
-// per PDE row its 1-D Lagrange factors along each axis ([NS][12]: x, y, z)
-__global__ void w1d_kernel(int64_t NS, int dim, const double *t64, double *w64, float *w32) {
+// per PDE row its 1-D Lagrange factors along each axis ([NS][12]: x, y, z,
+// 4 slots each, zeros past the np1 stencil nodes)
+__global__ void w1d_kernel(int64_t NS, int dim, int np1, const double *t64, double *w64, float *w32) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < NS; i += (int64_t)gridDim.x * blockDim.x) {
     for (int a = 0; a < 3; ++a) {
       double w[4] = {1.0, 0.0, 0.0, 0.0};
-      if (a < dim) cpm_lagrange4<double>(t64[3 * i + a], w);
+      if (a < dim) cpm_lagrange_rt<double>(np1, t64[3 * i + a], w);
       for (int k = 0; k < 4; ++k) {
         w64[i * 12 + 4 * a + k] = w[k];
         w32[i * 12 + 4 * a + k] = (float)w[k];
@@ -134,6 +135,8 @@ struct TArgs {
 };
 
 // b_c = s * sum of lambda over the rows whose unflipped FD slot points at c
+// (cs: right diagonal factor on the PDE entries of lambda, as in the forward
+// product: the kernels then apply A^T C)
 template <typename T>
 __global__ void __launch_bounds__(256) tb_kernel(TArgs<T> A, T s, const T *__restrict__ lam, T *__restrict__ bv,
                                                  int nrhs, int64_t ld) {
@@ -158,21 +161,21 @@ __global__ void __launch_bounds__(256) tb_kernel(TArgs<T> A, T s, const T *__res
 
 // y = R (d lambda_S + E^T b + remainder)
 template <typename T>
-__global__ void __launch_bounds__(256) ty_kernel(TArgs<T> A, T dg, T s, T rowscale, const T *__restrict__ lam,
+__global__ void __launch_bounds__(256) ty_kernel(TArgs<T> A, T dg, T s, T rowscale, T cs, const T *__restrict__ lam,
                                                  const T *__restrict__ bv, T *__restrict__ y, int nrhs, int64_t ld) {
   const int64_t NS = A.v.NS, N = NS + A.v.NC;
-  const int nz = (A.v.dim == 3) ? 4 : 1;
+  const int np1 = A.v.np1, nz = (A.v.dim == 3) ? np1 : 1;
   CPM_ROWS_COLS_LOOP(N, nrhs, j, r) {
     T acc = T(0);
     if (j < NS) {
-      acc = dg * __ldg(lam + j * ld + r);
+      acc = (dg * cs) * __ldg(lam + j * ld + r);
       const uint32_t rs = __ldg(A.rself + j);
       const int32_t b = (int32_t)(rs >> 9);
       const int l = (int)(rs & 511u);
       const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
       for (int cz = 0; cz < nz; ++cz)
-        for (int cy = 0; cy < 4; ++cy)
-          for (int cx = 0; cx < 4; ++cx) {
+        for (int cy = 0; cy < np1; ++cy)
+          for (int cx = 0; cx < np1; ++cx) {
             const int64_t key = loc_of(A.v, b, lx - cx, ly - cy, lz - cz);
             if (key < 0) continue;
             const int32_t cell = __ldg(A.cellid + key);
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(256) ty_kernel(TArgs<T> A, T dg, T s, T rowsca
     for (int32_t e = __ldg(A.T_ptr + j); e < e1; ++e) {
       const int64_t src = __ldg(A.T_src + e);
       const int kind = __ldg(A.T_kind + e);
-      if (kind == 0) acc += s * __ldg(lam + src * ld + r);
+      if (kind == 0) acc += (s * cs) * __ldg(lam + src * ld + r);
       else if (kind == 1) acc += __ldg(A.T_val + e) * __ldg(bv + src * ld + r);
       else acc += __ldg(A.T_val + e) * __ldg(lam + src * ld + r);
     }
@@ -225,7 +228,7 @@ cpm_status cpm_build_transpose(cpm_ctx *c) {
   TRY(cudaMemsetAsync(c->d_cellid, 0xFF, sizeof(int32_t) * std::max<int64_t>(nkeys, 1), st));
   TRY(cudaMalloc(&c->d_w1d64, sizeof(double) * 12 * std::max<int64_t>(c->NS, 1)));
   TRY(cudaMalloc(&c->d_w1d32, sizeof(float) * 12 * std::max<int64_t>(c->NS, 1)));
-  w1d_kernel<<<cpm_grid(c->NS, 256), 256, 0, st>>>(c->NS, c->dim, c->d_t64, c->d_w1d64, c->d_w1d32);
+  w1d_kernel<<<cpm_grid(c->NS, 256), 256, 0, st>>>(c->NS, c->dim, c->p + 1, c->d_t64, c->d_w1d64, c->d_w1d32);
   if (c->ncells > 0)
     cellid_kernel<<<cpm_grid(c->ncells, 256), 256, 0, st>>>(c->d_cell_key, c->ncells, c->d_cellid);
   TRY(cudaMalloc(&count, sizeof(int32_t) * (N + 1)));
@@ -258,11 +261,10 @@ done:
 }
 
 template <typename T>
-cpm_status cpm_apply_transpose_scaled_T(cpm_ctx *c, double m, double n, double rowscale, const T *u, T *v, int nrhs,
-                                        int64_t ld, cudaStream_t st) {
+cpm_status cpm_apply_transpose_rc_T(cpm_ctx *c, double m, double n, double rowscale, double colscale, const T *u,
+                                    T *v, int nrhs, int64_t ld, cudaStream_t st) {
   if (!c->transpose_ready) return CPM_ERR_STATE;
-  cpm_status rc = cpm_ensure(c->b_scratch, sizeof(T) * (size_t)c->NS * (size_t)ld);
-  if (rc) return rc;
+  if (sizeof(T) * (size_t)c->NS * (size_t)ld > c->b_scratch.bytes) return CPM_ERR_CAPACITY;
   TArgs<T> A;
   A.v = c->view();
   A.rself = c->d_rself;
@@ -285,22 +287,22 @@ cpm_status cpm_apply_transpose_scaled_T(cpm_ctx *c, double m, double n, double r
   const T s = T(n * inv_h2), dg = T(m + n * (-2.0 * c->dim * inv_h2));
   const int64_t N = c->NS + c->NC;
   cpm_prof_begin(c, st);
-  tb_kernel<T><<<cpm_grid(c->NS * nrhs, 256), 256, 0, st>>>(A, s, u, bv, nrhs, ld);
-  ty_kernel<T><<<cpm_grid(N * nrhs, 256), 256, 0, st>>>(A, dg, s, T(rowscale), u, bv, v, nrhs, ld);
+  tb_kernel<T><<<cpm_grid(c->NS * nrhs, 256), 256, 0, st>>>(A, T(s * T(colscale)), u, bv, nrhs, ld);
+  ty_kernel<T><<<cpm_grid(N * nrhs, 256), 256, 0, st>>>(A, dg, s, T(rowscale), T(colscale), u, bv, v, nrhs, ld);
   cpm_prof_end(c, st, c->NS * (int64_t)nrhs);
   cpm_count_launches(c, 2);
   CPM_CUDA_TRY(cudaGetLastError());
   return CPM_OK;
 }
-template cpm_status cpm_apply_transpose_scaled_T<double>(cpm_ctx *, double, double, double, const double *, double *,
-                                                         int, int64_t, cudaStream_t);
-template cpm_status cpm_apply_transpose_scaled_T<float>(cpm_ctx *, double, double, double, const float *, float *, int,
-                                                        int64_t, cudaStream_t);
+template cpm_status cpm_apply_transpose_rc_T<double>(cpm_ctx *, double, double, double, double, const double *,
+                                                     double *, int, int64_t, cudaStream_t);
+template cpm_status cpm_apply_transpose_rc_T<float>(cpm_ctx *, double, double, double, double, const float *,
+                                                    float *, int, int64_t, cudaStream_t);
 
 template <typename T>
 cpm_status cpm_apply_transpose_T(cpm_ctx *c, double m, double n, const T *u, T *v, int nrhs, int64_t ld,
                                  cudaStream_t st) {
-  return cpm_apply_transpose_scaled_T<T>(c, m, n, 1.0, u, v, nrhs, ld, st);
+  return cpm_apply_transpose_rc_T<T>(c, m, n, 1.0, 1.0, u, v, nrhs, ld, st);
 }
 template cpm_status cpm_apply_transpose_T<double>(cpm_ctx *, double, double, const double *, double *, int, int64_t,
                                                   cudaStream_t);

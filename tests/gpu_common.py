@@ -12,11 +12,11 @@ def need_gpu():
     return torch
 
 
-def pair(oracle_mod, workload, n_samples=None):
+def pair(oracle_mod, workload, n_samples=None, p=3):
     """(GPU band, oracle) for the same workload, boundary set on both."""
     from paper_2305_04711_gb300.cpm import Band
-    band = Band(workload.shape, workload.h).set_boundary(workload.curves, n_samples)
-    ref = oracle_mod.Oracle(workload.shape, workload.h).set_curves(workload.curves)
+    band = Band(workload.shape, workload.h, p=p).set_boundary(workload.curves, n_samples)
+    ref = oracle_mod.Oracle(workload.shape, workload.h, p=p).set_curves(workload.curves)
     return band, ref
 
 
