@@ -363,6 +363,7 @@ def apply_bandwidth(h, hbm, peak_src, log):
     out = {"workload": f"bumpy sphere (16 bumps, seed 0), h=1/{round(1 / h)}, no interior boundary",
            "rows": band.NS}
     for dt, bytes_row, key in ((torch.float32, BYTES_ROW_FP32, "fp32"), (torch.float64, BYTES_ROW_FP64, "fp64")):
+        tune = band.autotune(1, dt)
         u = torch.rand(band.N, dtype=dt, device="cuda")
         v = torch.empty_like(u)
         for _ in range(5):
@@ -375,7 +376,8 @@ def apply_bandwidth(h, hbm, peak_src, log):
         gbs = bytes_row * band.NS / (tms * 1e-3) / 1e9
         out[key] = {"ms": tms, "GB/s_algorithmic": gbs, "hbm_peak_GB/s": hbm, "frac": gbs / hbm,
                     "peak_source": peak_src, "bytes_per_row": bytes_row,
-                    "launches_per_product": p["launches"] / max(p["applies"], 1)}
+                    "launches_per_product": p["launches"] / max(p["applies"], 1),
+                    "gather": "per cell" if tune["gather1_per_cell"] else "per row"}
         if key == "fp64":
             out[key]["TFLOP/s"] = FLOPS_ROW_FP64 * band.NS / (tms * 1e-3) / 1e12
         del u, v
@@ -407,6 +409,9 @@ def run_ours(args):
     band = Band(wl.w.shape, wl.h).set_boundary(wl.w.curves, n_samples=wl.n_samples)
     band.reserve(NRHS, fp32_ir=True)
     log(f"band N={band.N} (NS={band.NS}, NC={band.NC})")
+    # launch shapes for this band and batch width (set-up, untimed)
+    tune = band.autotune(NRHS, torch.float32)
+    log(f"autotune: {tune}")
     _, cp_d = band.export_band()
     cp = cp_d.cpu().numpy()
     cpc = band.export_boundary()["cpc"].cpu().numpy()
@@ -476,7 +481,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "s/RHS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (FP64 solution, residual and refinement)", "data": "synthetic",
-            "config": wl.describe(band.N), "clocks": clocks, "e2e": e2e, "gpu_launches": int(prof["launches"])}
+            "config": wl.describe(band.N), "clocks": clocks, "e2e": e2e, "gpu_launches": int(prof["launches"]),
+            "autotune": tune}
     if rank == 0:
         last = stats[-1]
         line["solve"] = {"iterations": last.iterations, "fp64_iterations": last.fp64_iterations,

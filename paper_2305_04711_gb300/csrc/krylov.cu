@@ -29,13 +29,12 @@
 // layout) iterate together with their own scalars; a right-hand side that
 // converges is frozen.
 //
-// The FP32 form is mixed-precision iterative refinement by residual
-// replacement: FP32 BiCGSTAB (FP32 operator in its difference form, FP32
-// Krylov vectors) on the correction equation, its updates accumulated in the
-// FP64 solution; every time a column's FP32 residual has fallen by inner_tol
-// the FP64 residual f - A x replaces it, keeping the Krylov space (see
-// ir_reliable).  Convergence is decided on the FP64 residual only; a column
-// that stops gaining finishes in FP64.
+// The FP32 form is mixed-precision iterative refinement: FP32 BiCGSTAB (FP32
+// operator in its difference form, FP32 Krylov vectors) on the correction
+// equation, the correction added to the FP64 solution; every time a column's
+// FP32 residual has fallen by inner_tol the FP64 residual f - A x restarts it in
+// a fresh Krylov space (see ir_refine).  Convergence is decided
+// on the FP64 residual only; a column that stops gaining finishes in FP64.
 //
 // Workspaces are reserved by cpm_set_boundary / cpm_reserve; solves allocate
 // nothing.
@@ -65,32 +64,47 @@ enum {
   S_BEST, S_STALL, S_STOPPED, S_RN2_0, S_ITERS, NSC
 };
 
-enum { ST_OUT = 0, ST_INIT, ST_ALPHA, ST_OMEGA, ST_XR, ST_REPL };
+enum { ST_OUT = 0, ST_INIT, ST_ALPHA, ST_OMEGA, ST_XR };
 
 struct Red {
   double *part;      // [G][NQMAX][nrhs] block partials
   unsigned *ticket;  // arrival counter (reset by the last block)
   double *sc;        // [nrhs][NSC]
   double *out;       // [NQMAX][nrhs] reduced dot products (ST_OUT / ST_INIT)
-  const double *flag;  // [nrhs] per-column selection (ST_REPL)
   int nrhs;
 };
 
 struct Conv {
-  double tol;    // relative tolerance on the iterated system's residual
-  double stall;  // iterations without the residual halving before giving up
-  float mix;     // shadow-residual perturbation (0: rhat = r)
+  double tol;     // relative tolerance on the iterated system's residual
+  double stall;   // iterations without the residual halving before giving up
+  float mix;      // shadow = r o (1 + mix u) (shadow 0; mix 0: the classical rhat = r)
+  int shadow;     // 0: rhat from r as above; 1: rhat = u, independent of r
+  unsigned seed;  // of the hash u
 };
 
-// shadow-residual weight 1 + mix * u(i, c), u a fixed hash in [-1, 1]: with mix
-// in [0, 1) it keeps (rhat, r) > 0 while breaking the structure that drives
-// BiCGSTAB to near breakdown in FP32 (mix = 0: the classical rhat = r)
-__device__ __forceinline__ float shadow_weight(int64_t i, int c, float mix) {
-  if (mix == 0.0f) return 1.0f;
-  uint64_t k = (uint64_t)i * 0x9E3779B97F4A7C15ull + (uint64_t)c * 0xD1B54A32D192ED03ull;
+// a fixed hash u(i, c, seed) in [-1, 1]
+__device__ __forceinline__ float hash_unit(int64_t i, int c, unsigned seed) {
+  uint64_t k = (uint64_t)i * 0x9E3779B97F4A7C15ull + (uint64_t)c * 0xD1B54A32D192ED03ull +
+               (uint64_t)seed * 0x94D049BB133111EBull;
   k ^= k >> 31; k *= 0xBF58476D1CE4E5B9ull; k ^= k >> 29;
-  float u = (float)((k >> 40) & 0xFFFFFF) * (2.0f / 16777215.0f) - 1.0f;
-  return 1.0f + mix * u;
+  return (float)((k >> 40) & 0xFFFFFF) * (2.0f / 16777215.0f) - 1.0f;
+}
+
+// The shadow residual rhat of a (re)start, given the residual r there.
+// rhat = r is the classical choice, but when r is supported on few rows (a
+// right-hand side on the BC rows only) A r lives elsewhere and (rhat, A r) = 0:
+// the first step breaks down.  A random rhat (shadow 1) meets every row; its
+// (rhat, r) ~ |rhat| |r| / sqrt(N) is still far above the rounding of the dot
+// products.  `restarts` selects a fresh hash after a near-breakdown.
+__device__ __forceinline__ float shadow_of(const Conv &cv, int64_t i, int c, float r, unsigned restarts) {
+  if (cv.shadow == 1) return hash_unit(i, c, cv.seed + restarts);
+  if (cv.mix == 0.0f) return r;
+  return r * (1.0f + cv.mix * hash_unit(i, c, 0u));
+}
+__device__ __forceinline__ double shadow_of(const Conv &cv, int64_t i, int c, double r, unsigned restarts) {
+  if (cv.shadow == 1) return (double)hash_unit(i, c, cv.seed + restarts);
+  if (cv.mix == 0.0f) return r;
+  return r * (1.0 + (double)cv.mix * (double)hash_unit(i, c, 0u));
 }
 
 // ---- deterministic block reduction -----------------------------------------
@@ -148,42 +162,12 @@ __device__ void stage_finish(int stage, const Red &R, const Conv &cv, int c, con
     const double fn2 = d[1] > 0.0 ? d[1] : 1.0;
     s[S_FN2] = fn2;
     s[S_RN2] = d[0]; s[S_BEST] = d[0]; s[S_RN2_0] = d[0];
-    s[S_RHO] = d[0]; s[S_RHO_OLD] = 1.0; s[S_ALPHA] = 1.0; s[S_OMEGA] = 1.0; s[S_BETA] = 0.0;
+    s[S_RHO] = d[2]; s[S_RHO_OLD] = 1.0; s[S_ALPHA] = 1.0; s[S_OMEGA] = 1.0; s[S_BETA] = 0.0;
     s[S_RESTART] = 0.0; s[S_NRESTART] = 0.0; s[S_BROKE] = 0.0; s[S_STALL] = 0.0; s[S_STOPPED] = 0.0;
     s[S_ITERS] = 0.0;
     const bool fin = isfinite(d[0]);
     s[S_ACTIVE] = (!fin || sqrt(d[0]) <= cv.tol * sqrt(fn2)) ? 0.0 : 1.0;
     if (!fin) s[S_STOPPED] = 1.0;
-    return;
-  }
-  if (stage == ST_REPL) {
-    // residual replacement of a column whose recursion reached its reduction
-    // target: r now holds the (scaled) FP64 residual; the search direction p
-    // and the shadow residual stay, rho and beta follow the new r
-    if (R.flag[c] == 0.0) return;
-    double rho = d[0];
-    s[S_RESTART] = 0.0;
-    if (fabs(rho) <= 1e-28 * sqrt(d[2]) * sqrt(d[1]) || rho == 0.0) {
-      s[S_RESTART] = 1.0;
-      s[S_NRESTART] += 1.0;
-      rho = (cv.mix != 0.0f) ? d[3] : d[1];
-      s[S_RHO] = 1.0; s[S_ALPHA] = 1.0; s[S_OMEGA] = 1.0;
-    }
-    double beta = (rho / s[S_RHO]) * (s[S_ALPHA] / s[S_OMEGA]);
-    if (!isfinite(beta) || s[S_BROKE] != 0.0) {
-      // the recursion broke down before: restart the Krylov space from r
-      s[S_RESTART] = 1.0;
-      rho = (cv.mix != 0.0f) ? d[3] : d[1];
-      s[S_RHO] = 1.0; s[S_ALPHA] = 1.0; s[S_OMEGA] = 1.0;
-      beta = 0.0;
-      s[S_BROKE] = 0.0;
-    }
-    s[S_BETA] = beta;
-    s[S_RHO_OLD] = s[S_RHO];
-    s[S_RHO] = rho;
-    s[S_FN2] = d[1] > 0.0 ? d[1] : 1.0;
-    s[S_RN2] = d[1]; s[S_BEST] = d[1]; s[S_STALL] = 0.0; s[S_STOPPED] = 0.0;
-    s[S_ACTIVE] = (d[1] > 0.0 && isfinite(d[1])) ? 1.0 : 0.0;
     return;
   }
   if (s[S_ACTIVE] == 0.0) return;
@@ -212,11 +196,12 @@ __device__ void stage_finish(int stage, const Red &R, const Conv &cv, int c, con
   double rho = d[1];
   s[S_RESTART] = 0.0;
   if (fabs(rho) <= 1e-28 * sqrt(d[2]) * sqrt(rn2) || rho == 0.0) {
-    // restart the shadow residual: rhat = w r, p = r, rho = (w r, r)
+    // restart from a new shadow residual (the one the XR pass dotted with r
+    // as d[3]): p = r, rho = (rhat', r)
     s[S_RESTART] = 1.0;
     s[S_NRESTART] += 1.0;
     if (s[S_NRESTART] > 20.0) { s[S_BROKE] = 1.0; s[S_ACTIVE] = 0.0; return; }
-    rho = (cv.mix != 0.0f) ? d[3] : rn2;
+    rho = d[3];
     s[S_RHO] = 1.0; s[S_ALPHA] = 1.0; s[S_OMEGA] = 1.0;
   }
   s[S_BETA] = (rho / s[S_RHO]) * (s[S_ALPHA] / s[S_OMEGA]);
@@ -296,14 +281,15 @@ __device__ __forceinline__ void vloop(const Body &body, int64_t N, int nrhs, int
 // ---- iteration kernels -------------------------------------------------------
 template <typename T>
 struct PBody {
-  const double *sc; float mix;
+  const double *sc; Conv cv;
   const T *__restrict__ r; T *__restrict__ rh; T *__restrict__ p; const T *__restrict__ v;
-  mutable int c_; mutable bool restart; mutable T beta, omega;
+  mutable int c_; mutable bool restart; mutable unsigned nres; mutable T beta, omega;
   struct Elt { T r, p, v; };
   __device__ bool on(int c) const { return sc[c * NSC + S_ACTIVE] != 0.0; }
   __device__ void init(int c) const {
     c_ = c;
     restart = sc[c * NSC + S_RESTART] != 0.0;
+    nres = (unsigned)sc[c * NSC + S_NRESTART];
     beta = T(sc[c * NSC + S_BETA]);
     omega = T(sc[c * NSC + S_OMEGA]);
   }
@@ -313,7 +299,7 @@ struct PBody {
   }
   __device__ void apply(Elt &e, int64_t i, int64_t o, T (&)[1]) const {
     if (restart) {
-      rh[o] = e.r * T(shadow_weight(i, c_, mix));
+      rh[o] = shadow_of(cv, i, c_, e.r, nres);
       p[o] = e.r;
     } else {
       p[o] = e.r + beta * (e.p - omega * e.v);
@@ -322,9 +308,9 @@ struct PBody {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(KT, 2) kp_kernel(const double *sc, float mix, int64_t N, int nrhs, int64_t ld,
+__global__ void __launch_bounds__(KT, 2) kp_kernel(const double *sc, Conv cv, int64_t N, int nrhs, int64_t ld,
                                                 const T *r, T *rh, T *p, const T *v) {
-  PBody<T> b{sc, mix, r, rh, p, v};
+  PBody<T> b{sc, cv, r, rh, p, v};
   double acc[1];
   vloop<T, 1>(b, N, nrhs, ld, acc);
 }
@@ -376,14 +362,15 @@ __global__ void __launch_bounds__(KT, 2) dot_kernel(Red R, Conv cv, int stage, i
 // x += D (alpha p + omega s);  r = s - omega t;  the XR dot products
 template <typename T, typename TX>
 struct XRBody {
-  const double *sc; float mix; int64_t NS; T cs;
+  const double *sc; Conv cv; int64_t NS; T cs;
   TX *__restrict__ x; T *__restrict__ r; const T *__restrict__ rh; const T *__restrict__ p;
   const T *__restrict__ s; const T *__restrict__ t;
-  mutable int c_; mutable T alpha, omega;
+  mutable int c_; mutable unsigned nres; mutable T alpha, omega;
   struct Elt { TX x; T rh, p, s, t; };
   __device__ bool on(int c) const { return sc[c * NSC + S_ACTIVE] != 0.0; }
   __device__ void init(int c) const {
     c_ = c;
+    nres = (unsigned)sc[c * NSC + S_NRESTART] + 1u;
     alpha = T(sc[c * NSC + S_ALPHA]);
     omega = T(sc[c * NSC + S_OMEGA]);
   }
@@ -398,44 +385,48 @@ struct XRBody {
     run[0] += rn * rn;
     run[1] += e.rh * rn;
     run[2] += e.rh * e.rh;
-    if (mix != 0.0f) run[3] += T(shadow_weight(i, c_, mix)) * rn * rn;
+    // (rhat', r) for the shadow residual a restart would take
+    run[3] += shadow_of(cv, i, c_, rn, nres) * rn;
   }
 };
 
 template <typename T, typename TX>
 __global__ void __launch_bounds__(KT, 2) kxr_kernel(Red R, Conv cv, int64_t N, int64_t NS, T cs, int64_t ld, TX *x,
                                                  T *r, const T *rh, const T *p, const T *s, const T *t) {
-  XRBody<T, TX> body{R.sc, cv.mix, NS, cs, x, r, rh, p, s, t};
+  XRBody<T, TX> body{R.sc, cv, NS, cs, x, r, rh, p, s, t};
   double acc[4];
   vloop<T, 4>(body, N, R.nrhs, ld, acc);
   if (block_publish<4>(acc, R)) finish_reduce<4>(ST_XR, R, cv);
 }
 
-// r = f - r (r holds A x, or nothing when x = 0);  rhat = r;  p = v = 0;
-// (r, r), (f, f) -> the initial scalars
+// r = f - r (r holds A x, or nothing when x = 0);  rhat = shadow of r;
+// p = v = 0;  (r, r), (f, f), (rhat, r) -> the initial scalars
 template <typename T>
 struct InitBody {
   const T *__restrict__ f; T *__restrict__ r; T *__restrict__ rh; T *__restrict__ p; T *__restrict__ v;
-  bool x_zero;
+  bool x_zero; Conv cv;
+  mutable int c_;
   struct Elt { T f, r; };
   __device__ bool on(int) const { return true; }
-  __device__ void init(int) const {}
+  __device__ void init(int c) const { c_ = c; }
   __device__ void load(Elt &e, int64_t, int64_t o) const { e.f = f[o]; e.r = x_zero ? T(0) : r[o]; }
-  __device__ void apply(Elt &e, int64_t, int64_t o, T (&run)[2]) const {
+  __device__ void apply(Elt &e, int64_t i, int64_t o, T (&run)[3]) const {
     const T rv = e.f - e.r;
-    r[o] = rv; rh[o] = rv; p[o] = T(0); v[o] = T(0);
+    const T sh = shadow_of(cv, i, c_, rv, 0u);
+    r[o] = rv; rh[o] = sh; p[o] = T(0); v[o] = T(0);
     run[0] += rv * rv;
     run[1] += e.f * e.f;
+    run[2] += sh * rv;
   }
 };
 
 template <typename T>
 __global__ void __launch_bounds__(KT, 2) init_kernel(Red R, Conv cv, int64_t N, int64_t ld, bool x_zero, const T *f,
                                                   T *r, T *rh, T *p, T *v) {
-  InitBody<T> body{f, r, rh, p, v, x_zero};
-  double acc[2];
-  vloop<T, 2>(body, N, R.nrhs, ld, acc);
-  if (block_publish<2>(acc, R)) finish_reduce<2>(ST_INIT, R, cv);
+  InitBody<T> body{f, r, rh, p, v, x_zero, cv};
+  double acc[3];
+  vloop<T, 3>(body, N, R.nrhs, ld, acc);
+  if (block_publish<3>(acc, R)) finish_reduce<3>(ST_INIT, R, cv);
 }
 
 // ---- FP64 residual -----------------------------------------------------------
@@ -461,7 +452,7 @@ __global__ void __launch_bounds__(KT, 2) resid_kernel(Red R, int64_t N, int64_t 
   ResidBody body{f, r, NS, w2};
   double acc[2];
   vloop<double, 2>(body, N, R.nrhs, ld, acc);
-  Conv cv{0.0, 0.0, 0.0f};
+  Conv cv{0.0, 0.0, 0.0f, 0, 0u};
   if (block_publish<2>(acc, R)) finish_reduce<2>(ST_OUT, R, cv);
 }
 
@@ -493,38 +484,8 @@ __global__ void __launch_bounds__(KT, 2) wnorm_kernel(Red R, int64_t N, int64_t 
   WNormBody body{y, NS, w2};
   double acc[1];
   vloop<double, 1>(body, N, R.nrhs, ld, acc);
-  Conv cv{0.0, 0.0, 0.0f};
+  Conv cv{0.0, 0.0, 0.0f, 0, 0u};
   if (block_publish<1>(acc, R)) finish_reduce<1>(ST_OUT, R, cv);
-}
-
-// residual replacement: r = (float) (W r64) on the selected columns (W = wrow
-// on PDE rows, 1 on BC rows); (rhat, r), (r, r), (rhat, rhat), (w r, r)
-template <typename T>
-struct ReplBody {
-  const double *flag; const double *__restrict__ r64; T *__restrict__ r; const T *__restrict__ rh;
-  int64_t NS; double wrow; float mix;
-  mutable int c_;
-  struct Elt { double r64; T rh; };
-  __device__ bool on(int c) const { return flag[c] != 0.0; }
-  __device__ void init(int c) const { c_ = c; }
-  __device__ void load(Elt &e, int64_t, int64_t o) const { e.r64 = r64[o]; e.rh = rh[o]; }
-  __device__ void apply(Elt &e, int64_t i, int64_t o, T (&run)[4]) const {
-    const T rv = T(((i < NS) ? wrow : 1.0) * e.r64);
-    r[o] = rv;
-    run[0] += e.rh * rv;
-    run[1] += rv * rv;
-    run[2] += e.rh * e.rh;
-    if (mix != 0.0f) run[3] += T(shadow_weight(i, c_, mix)) * rv * rv;
-  }
-};
-
-template <typename T>
-__global__ void __launch_bounds__(KT, 2) repl_kernel(Red R, Conv cv, int64_t N, int64_t NS, double wrow, int64_t ld,
-                                                     const double *r64, T *r, const T *rh) {
-  ReplBody<T> body{R.flag, r64, r, rh, NS, wrow, cv.mix};
-  double acc[4];
-  vloop<T, 4>(body, N, R.nrhs, ld, acc);
-  if (block_publish<4>(acc, R)) finish_reduce<4>(ST_REPL, R, cv);
 }
 
 // out = W f (PDE rows scaled by dS)
@@ -536,32 +497,23 @@ __global__ void scale_rows64_kernel(int64_t N, int64_t NS, int nrhs, int64_t ld,
   }
 }
 
-// columns with acc != 0 take the candidate
-__global__ void accept_kernel(int64_t N, int nrhs, int64_t ld, const double *acc, const double *xc, double *x) {
-  CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
-    int64_t o = i * ld + c;
-    if (acc[c] != 0.0) x[o] = xc[o];
-  }
-}
-
-// restarted refinement: FP32 right-hand side W r / |W r| per active column
-// (scale 0: inactive column, zero right-hand side)
+// refinement step: FP32 right-hand side W r / scale per selected column (scale
+// 0: a column left out, zero right-hand side) and a zero correction d
 __global__ void ir_rhs_kernel(int64_t N, int64_t NS, double wrow, int nrhs, int64_t ld, const double *scale,
-                              const double *r64, float *f32) {
+                              const double *r64, float *f32, float *d32) {
   CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
     int64_t o = i * ld + c;
     double sc = scale[c];
     f32[o] = (sc > 0.0) ? (float)(((i < NS) ? wrow : 1.0) * r64[o] / sc) : 0.0f;
+    d32[o] = 0.0f;
   }
 }
 
-// candidate xc = x + scale * d (FP64 accumulation of the FP32 correction)
-__global__ void ir_candidate_kernel(int64_t N, int nrhs, int64_t ld, const double *scale, const double *d,
-                                    const double *x, double *xc) {
+// x += d: the FP32 correction of an inner solve into the FP64 solution
+__global__ void ir_add_kernel(int64_t N, int nrhs, int64_t ld, const float *d32, double *x) {
   CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
     int64_t o = i * ld + c;
-    double sc = scale[c];
-    xc[o] = (sc > 0.0) ? x[o] + sc * d[o] : x[o];
+    x[o] += (double)d32[o];
   }
 }
 
@@ -572,6 +524,8 @@ struct GraphKey {
   const void *fn = nullptr;
   double m = 0, n = 0, rs = 0, cs = 0, tol = 0, stall = 0;
   float mix = 0;
+  int shadow = 0;
+  unsigned seed = 0;
   const void *x = nullptr, *vecs = nullptr;
   int nrhs = 0, steps = 0, elem = 0, xelem = 0, G = 0;
   int64_t ld = 0;
@@ -583,9 +537,9 @@ struct SolveWork {
   bool has32 = false;
   double *v64[6] = {};       // FP64 Krylov vectors (FP64 solves, FP64 finish of FP32_IR)
   float *v32[6] = {};        // FP32 Krylov vectors (FP32_IR inner solves)
+  float *d32 = nullptr;      // FP32_IR correction of one inner solve
   double *r64 = nullptr;     // FP64 residual
-  double *xc = nullptr;      // FP32_IR candidate iterate
-  double *xd = nullptr;      // FP32_IR FP64 accumulator of the inner solution
+  double *xc = nullptr;      // FP64 scratch of the rounding-floor estimate
   double *part = nullptr, *sc = nullptr, *out = nullptr, *cols = nullptr;
   unsigned *ticket = nullptr;
   double *h_pin = nullptr;   // host mirror: [NSC * ld] scalars, then [NQMAX * ld] dots
@@ -600,7 +554,8 @@ static void free_work(SolveWork *w) {
   if (!w) return;
   for (auto p : w->v64) cudaFree(p);
   for (auto p : w->v32) cudaFree(p);
-  cudaFree(w->r64); cudaFree(w->xc); cudaFree(w->xd);
+  cudaFree(w->d32);
+  cudaFree(w->r64); cudaFree(w->xc);
   cudaFree(w->part); cudaFree(w->sc); cudaFree(w->out); cudaFree(w->cols); cudaFree(w->ticket);
   if (w->h_pin) cudaFreeHost(w->h_pin);
   if (w->gexec) cudaGraphExecDestroy(w->gexec);
@@ -633,8 +588,8 @@ cpm_status cpm_reserve_solve(cpm_ctx *c, int64_t ld, bool fp32) {
   al((void **)&w->r64, n * sizeof(double));
   if (fp32) {
     for (auto &p : w->v32) al((void **)&p, n * sizeof(float));
+    al((void **)&w->d32, n * sizeof(float));
     al((void **)&w->xc, n * sizeof(double));
-    al((void **)&w->xd, n * sizeof(double));
   }
   w->G = 2 * c->nsm;
   // partials for up to 4 blocks per SM (the autotuner's widest choice)
@@ -673,7 +628,7 @@ struct Op {
 template <typename T>
 struct Vecs { T *r, *rh, *p, *v, *s, *t; };
 
-Red red_of(SolveWork *w, int nrhs) { return Red{w->part, w->ticket, w->sc, w->out, w->cols, nrhs}; }
+Red red_of(SolveWork *w, int nrhs) { return Red{w->part, w->ticket, w->sc, w->out, nrhs}; }
 
 // one BiCGSTAB iteration for all active columns (device only)
 template <typename T, typename TX>
@@ -682,7 +637,7 @@ cpm_status iteration(cpm_ctx *c, const Op<T> &op, TX *x, const Vecs<T> &V, Solve
   const int64_t N = c->NS + c->NC;
   const Red R = red_of(w, nrhs);
   const unsigned G = (unsigned)w->G;
-  kp_kernel<T><<<G, KT, 0, st>>>(w->sc, cv.mix, N, nrhs, ld, V.r, V.rh, V.p, V.v);
+  kp_kernel<T><<<G, KT, 0, st>>>(w->sc, cv, N, nrhs, ld, V.r, V.rh, V.p, V.v);
   cpm_status rc = op(c, V.p, V.v, nrhs, ld, st, false);
   if (rc) return rc;
   dot_kernel<T, 1><<<G, KT, 0, st>>>(R, cv, ST_ALPHA, N, ld, V.rh, V.v);
@@ -710,7 +665,8 @@ cpm_status iterations(cpm_ctx *c, const Op<T> &op, TX *x, const Vecs<T> &V, Solv
     GraphKey k;
     std::memset(&k, 0, sizeof(k));
     k.fn = (const void *)op.fn; k.m = op.m; k.n = op.n; k.rs = op.rowscale; k.cs = op.colscale;
-    k.tol = cv.tol; k.stall = cv.stall; k.mix = cv.mix; k.x = x; k.vecs = V.r; k.nrhs = nrhs; k.steps = steps;
+    k.tol = cv.tol; k.stall = cv.stall; k.mix = cv.mix; k.shadow = cv.shadow; k.seed = cv.seed;
+    k.x = x; k.vecs = V.r; k.nrhs = nrhs; k.steps = steps;
     k.elem = (int)sizeof(T); k.xelem = (int)sizeof(TX); k.ld = ld; k.G = w->G;
     if (!(w->gexec && w->gkey == k)) {
       if (w->gexec) { cudaGraphExecDestroy(w->gexec); w->gexec = nullptr; }
@@ -868,23 +824,24 @@ double worst_relres(const std::vector<double> &rn2, const std::vector<double> &f
   return worst;
 }
 
-// Mixed-precision iterative refinement by residual replacement ("reliable
-// updates"): one FP32 BiCGSTAB runs on the correction equation (the iterated
-// form of A d = r), its updates accumulated straight into the FP64 solution x.
-// Whenever a column's recursive FP32 residual has dropped by `delta` relative
-// to its last replacement, the host computes the FP64 residual r = f - A x
-// (difference-form product, accurate to the FP64 rounding of local
-// differences), stops the columns that meet tol there, and replaces the FP32
-// residual of the others by r (scaled as the iterated form needs), keeping the
-// search direction p and the shadow residual: the Krylov space survives the
-// refinement step, unlike a restarted inner solve, so the FP32 iteration count
-// stays close to an FP64 solve's.  Each replacement bounds the gap between the
-// recursive and the true residual, which the FP32 operator's rounding (about
-// eps_32 times the stencil's local amplification) otherwise lets grow.  A
-// column whose FP64 residual fails to fall over three replacements is left for
-// the FP64 finish.  rhs_w weights the PDE rows of the FP32 residual: the
-// scaling of the left-scaled form, or 1 for a right-preconditioned form.
-cpm_status ir_reliable(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, double m, double n,
+// Mixed-precision iterative refinement: FP32 BiCGSTAB on the correction
+// equation (the iterated form of A d = r), d accumulated in FP32 and added to
+// the FP64 solution x at each refinement.  Whenever a column's recursive FP32 residual has dropped by
+// `delta` relative to the start of the inner solve, the host computes the FP64
+// residual r = f - A x (difference-form product, accurate to the FP64 rounding
+// of local differences), stops the columns that meet tol there, and restarts
+// the FP32 iteration of the others from r (scaled as the iterated form needs)
+// with a fresh Krylov space: p = 0 and a random shadow residual.  Keeping p and
+// rhat across the refinement (residual replacement) was tried and lets FP32
+// BiCGSTAB drift into large residual spikes on fine torus grids after a few
+// hundred iterations (the bi-orthogonality of an old shadow residual is lost in
+// FP32), whereas fresh inner solves of about a hundred iterations each reduce
+// the FP64 residual by delta steadily.  The random shadow matters: the first
+// residual lives on the BC rows only, so rhat = r gives (rhat, A r) = 0.  A
+// column whose FP64 residual fails to fall over three refinements is left for
+// the FP64 finish.  rhs_w weights the PDE rows of the FP32 residual: the scaling
+// of the left-scaled form, or 1 for a right-preconditioned form.
+cpm_status ir_refine(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, double m, double n,
                        const double *f, double *x, SolveWork *w, int nrhs, int64_t ld, double wrow, double rhs_w,
                        double tol, double delta, int maxit, int max_repl, int check_every, bool trace, int *iters,
                        int *nrepl_out, int *restarts, std::vector<double> &rn2, std::vector<double> &fn2,
@@ -893,7 +850,7 @@ cpm_status ir_reliable(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, 
   const unsigned g = cpm_grid(N * nrhs, 256);
   Vecs<float> V{w->v32[0], w->v32[1], w->v32[2], w->v32[3], w->v32[4], w->v32[5]};
   float *f32 = w->v32[5];  // first right-hand side: read by the init kernel before t is written
-  const Conv cv{delta, 4000.0, 0.5f};
+  const Conv cv{delta, 400.0, 0.0f, 1, 1u};
   const Red R = red_of(w, nrhs);
   std::vector<double> flag(nrhs, 0.0), best(nrhs, INFINITY);
   std::vector<int> stall(nrhs, 0);
@@ -901,7 +858,6 @@ cpm_status ir_reliable(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, 
   cpm_status rc = residual64(c, ap64, m, n, f, x, w, nrhs, ld, wrow, rn2, fn2, st);
   if (rc) return rc;
   int it_total = 0, nrep = 0, nrs = 0;
-  bool first = true;
   while (true) {
     // the rounding floor matters once the residual nears the tolerance
     if (worst_relres(rn2, fn2) > tol && worst_relres(rn2, fn2) < 1e3 * tol) {
@@ -918,28 +874,25 @@ cpm_status ir_reliable(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, 
       any = true;
     }
     if (trace)
-      std::fprintf(stderr, "[cpm ru] replacement %d it %d relres[0] %.3e worst %.3e\n", nrep, it_total,
+      std::fprintf(stderr, "[cpm ir] refinement %d it %d relres[0] %.3e worst %.3e\n", nrep, it_total,
                    relres_of(rn2[0], fn2[0]), worst_relres(rn2, fn2));
     if (!any || it_total >= maxit || nrep >= max_repl) break;
     CPM_CUDA_TRY(cudaMemcpyAsync(w->cols, flag.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-    if (first) {
-      // r = W r64 on the selected columns (0 elsewhere), rhat = r, p = v = 0
-      ir_rhs_kernel<<<g, 256, 0, st>>>(N, c->NS, rhs_w, nrhs, ld, w->cols, w->r64, f32);
-      init_kernel<float><<<(unsigned)w->G, KT, 0, st>>>(R, cv, N, ld, true, f32, V.r, V.rh, V.p, V.v);
-      cpm_count_launches(c, 2);
-      first = false;
-    } else {
-      repl_kernel<float><<<(unsigned)w->G, KT, 0, st>>>(R, cv, N, c->NS, rhs_w, ld, w->r64, V.r, V.rh);
-      cpm_count_launches(c, 1);
-    }
+    // r = W r64 on the selected columns (0 elsewhere), d = 0, a fresh Krylov
+    // space; the correction accumulates in FP32 (it is needed to about delta)
+    ir_rhs_kernel<<<g, 256, 0, st>>>(N, c->NS, rhs_w, nrhs, ld, w->cols, w->r64, f32, w->d32);
+    init_kernel<float><<<(unsigned)w->G, KT, 0, st>>>(R, cv, N, ld, true, f32, V.r, V.rh, V.p, V.v);
+    cpm_count_launches(c, 2);
     ++nrep;
     int it = 0, rs = 0;
     bool broke = false;
-    rc = krylov_run<float, double>(c, op32, x, V, w, nrhs, ld, cv, maxit - it_total, check_every, &it, &rs, &broke,
-                                   st);
+    rc = krylov_run<float, float>(c, op32, w->d32, V, w, nrhs, ld, cv, maxit - it_total, check_every, &it, &rs,
+                                  &broke, st);
     if (rc) return rc;
+    ir_add_kernel<<<g, 256, 0, st>>>(N, nrhs, ld, w->d32, x);
+    cpm_count_launches(c, 1);
     it_total += it;
-    nrs = rs;
+    nrs += rs;
     rc = residual64(c, ap64, m, n, f, x, w, nrhs, ld, wrow, rn2, fn2, st);
     if (rc) return rc;
   }
@@ -960,7 +913,7 @@ cpm_status fp64_passes(cpm_ctx *c, ApplyFn<double> ap64, bool left, double dS, d
   const int64_t N = c->NS + c->NC;
   Vecs<double> V{w->v64[0], w->v64[1], w->v64[2], w->v64[3], w->v64[4], w->v64[5]};
   const Op<double> op = left ? Op<double>{ap64, m, n, dS, 1.0} : Op<double>{ap64, m, n, 1.0, dS};
-  const Conv cv{tol, 4000.0, 0.0f};
+  const Conv cv{tol, 4000.0, 0.0f, 0, 0u};  // classical rhat = r (restarted on a first-step breakdown)
   double prev_worst = INFINITY;
   for (int pass = 0; pass < 6; ++pass) {
     const double *rhs = f;
@@ -1051,7 +1004,7 @@ cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const double
     // balanced), the adjoint right-preconditioned; the requested norm decides
     // acceptance and convergence
     const Op<float> op32 = adjoint ? Op<float>{ap32, m, n, 1.0, dS} : Op<float>{ap32, m, n, dS, 1.0};
-    rc = ir_reliable(c, ap64, op32, m, n, f, x, w, nrhs, ld, wrow, adjoint ? 1.0 : dS, opts.tol, opts.inner_tol,
+    rc = ir_refine(c, ap64, op32, m, n, f, x, w, nrhs, ld, wrow, adjoint ? 1.0 : dS, opts.tol, opts.inner_tol,
                      opts.maxit, opts.max_refine, opts.check_every, trace, &iters, &refinements, &restarts, rn2, fn2,
                      floors, st);
     if (rc) return rc;
@@ -1121,7 +1074,7 @@ cpm_status cpm_time_vector_kernels(cpm_ctx *c, int prec, int nrhs, int64_t ld, i
   if (!w || ld > w->ld || (prec == CPM_PREC_FP32 && !w->has32) || G < 1 || G > 4 * c->nsm) return CPM_ERR_CAPACITY;
   const int64_t N = c->NS + c->NC;
   Red R = red_of(w, nrhs);
-  const Conv cv{0.0, 0.0, 0.0f};
+  const Conv cv{0.0, 0.0, 0.0f, 0, 0u};
   cudaEvent_t e0, e1;
   CPM_CUDA_TRY(cudaEventCreate(&e0));
   CPM_CUDA_TRY(cudaEventCreate(&e1));
