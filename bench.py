@@ -377,7 +377,8 @@ def apply_bandwidth(h, hbm, peak_src, log):
         out[key] = {"ms": tms, "GB/s_algorithmic": gbs, "hbm_peak_GB/s": hbm, "frac": gbs / hbm,
                     "peak_source": peak_src, "bytes_per_row": bytes_row,
                     "launches_per_product": p["launches"] / max(p["applies"], 1),
-                    "gather": "per cell" if tune["gather1_per_cell"] else "per row"}
+                    "single_mode": {0: "fused", 1: "per-cell gather + combine",
+                                    2: "per-row gather + combine"}[tune["single_mode"]]}
         if key == "fp64":
             out[key]["TFLOP/s"] = FLOPS_ROW_FP64 * band.NS / (tms * 1e-3) / 1e12
         del u, v

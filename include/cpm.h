@@ -129,10 +129,12 @@ typedef struct {
                         floor grows like 1/h^2) */
   int maxit;         /* BiCGSTAB iterations (both modes) */
   int mode;          /* cpm_solve_mode */
-  double inner_tol;  /* FP32_IR: reduction in (0,1) of a column's FP32 recursive residual after
-                        which its FP64 residual replaces it, i.e. what one refinement step aims
-                        for (0 -> 1e-2) */
-  int max_refine;    /* FP32_IR: maximum number of refinement (residual replacement) steps (0 -> 200) */
+  double inner_tol;  /* FP32_IR: reduction in (0,1) of a column's FP32 recursive residual at
+                        which its inner solve ends and the FP64 residual restarts it, i.e. what
+                        one refinement step aims for (0 -> 1e-1; the FP32 product's rounding,
+                        relative to the smallest eigenvalues, limits what one inner solve can
+                        gain on fine grids) */
+  int max_refine;    /* FP32_IR: maximum number of refinement steps (0 -> 200) */
   int check_every;   /* iterations between host convergence checks (0 -> 16) */
   int norm;          /* cpm_norm.  PLAIN is the paper's right-preconditioned form with the unscaled
                         residual; SCALED iterates on the row-scaled system W A x = W f */
@@ -289,14 +291,14 @@ cpm_status cpm_surface_divergence(cpm_ctx *ctx, const double *X_dev, double *b_d
 /* Solves A x = f with diagonal-preconditioned BiCGSTAB (Sec. 5.4), preconditioner
  * diag(m I + n diag L) on PDE rows and 1 on BC rows.  x_dev holds the initial
  * guess on entry.  FP64 mode iterates in FP64.  FP32_IR is mixed-precision
- * iterative refinement by residual replacement: FP32 BiCGSTAB (FP32 operator and
- * Krylov vectors) iterates on the correction equation with its updates added to
- * x in FP64; whenever a right-hand side's FP32 residual has fallen by
- * inner_tol, the FP64 residual r = f - A x replaces it (the search direction
- * and shadow residual are kept), and the right-hand side stops once r meets
- * tol.  One whose FP64 residual stops falling is finished by FP64 BiCGSTAB from
- * its current iterate, so the result always meets tol in FP64.  All right-hand sides of a batch iterate together with
- * their own scalars; every dot product is reduced on the device in a fixed
+ * iterative refinement: FP32 BiCGSTAB (FP32 operator and Krylov vectors)
+ * iterates on the correction equation, the correction accumulated in FP32 and
+ * added to x in FP64; whenever a right-hand side's FP32 residual has fallen by
+ * inner_tol, the FP64 residual r = f - A x restarts its inner solve in a fresh
+ * Krylov space (random shadow residual), and the right-hand side stops once r
+ * meets tol.  One whose FP64 residual stops falling is finished by FP64
+ * BiCGSTAB from its current iterate, so the result always meets tol in FP64.
+ * All right-hand sides of a batch iterate together with their own scalars; every dot product is reduced on the device in a fixed
  * order (results do not depend on scheduling), and groups of check_every
  * iterations are replayed from a captured CUDA graph on the context's internal
  * stream, which is ordered after the caller's prior work on `stream` and before
@@ -345,7 +347,8 @@ typedef struct {
   int cells_blocks_per_sm;   /* grid cap of the cell gather, blocks of 8 warps per SM (0: default 16) */
   int combine_warps_per_sm;  /* grid cap of the warp-per-row combine (0: default 64) */
   int vec_blocks_per_sm;     /* blocks of 512 threads per SM of the Krylov vector kernels (1, 2 or 4) */
-  int gather1_per_cell;      /* single right-hand side gather: 1 = one thread per stencil cell, 0 = per row */
+  int single_mode;           /* single right-hand side product: 0 = fused persistent kernel, 1 = per-cell gather
+                              * then combine, 2 = per-row gather then combine */
   double product_ms;         /* one operator product with the chosen shapes */
   double product_ms_default; /* the same with the built-in defaults */
   double vector_ms;          /* one two-product reduction over [N][ld] with the chosen blocks */
@@ -366,12 +369,12 @@ cpm_status cpm_autotune(cpm_ctx *ctx, int nrhs, int64_t ld, int prec, cpm_tune_i
 /* Sets the launch shapes directly (for instance to reuse a tuned choice in a
  * new context of the same band, or to exercise one candidate): cells_xh applies
  * to batches of nrhs columns in precision prec; cells_blocks_per_sm,
- * combine_warps_per_sm, vec_blocks_per_sm and gather1_per_cell to every later
+ * combine_warps_per_sm, vec_blocks_per_sm and single_mode to every later
  * product and solve.  A zero field restores that field's default; the timing
  * fields are ignored.  Host-only, no stream work.  Errors: ARG (an x pass count
  * that does not divide the stencil width or that the precision does not hold in
  * registers, a grid cap outside 1..256, vec_blocks_per_sm outside 0..4,
- * gather1_per_cell not 0 or 1), STATE (before cpm_set_boundary). */
+ * single_mode outside 0..2), STATE (before cpm_set_boundary). */
 cpm_status cpm_set_tune(cpm_ctx *ctx, int nrhs, int prec, const cpm_tune_info *info);
 
 /* Diagnostics: counts of crossing-test flips that found no BC twin (Sec. 4.2;

@@ -50,7 +50,7 @@ class SolveOpts(ctypes.Structure):
 class TuneInfo(ctypes.Structure):
     _fields_ = [("cells_xh", ctypes.c_int), ("cells_blocks_per_sm", ctypes.c_int),
                 ("combine_warps_per_sm", ctypes.c_int), ("vec_blocks_per_sm", ctypes.c_int),
-                ("gather1_per_cell", ctypes.c_int),
+                ("single_mode", ctypes.c_int),
                 ("product_ms", ctypes.c_double), ("product_ms_default", ctypes.c_double),
                 ("vector_ms", ctypes.c_double)]
 

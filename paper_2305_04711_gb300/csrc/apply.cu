@@ -479,8 +479,15 @@ cpm_status cpm_apply_rc_T(cpm_ctx *c, double m, double n, double rowscale, doubl
   else if (nrhs >= 16 && nrhs <= 32)
     launched = launch_batched<T, 1>(c, A, (T)m, (T)n, (T)rowscale, cs, u, a, v, nrhs, ld, st, diff);
   else if (nrhs == 1 && c->ncells > 0) {
-    launched = 1 + cpm_launch_gather1<T>(c, A, cs, u, a, st, diff);
-    cpm_launch_combine<T>(A, (T)m, (T)n, (T)rowscale, cs, u, a, v, nrhs, ld, st, diff);
+    // default: the fused persistent product; 1 and 2: per-cell or per-row
+    // gather, then the combine
+    launched = (c->tune.single_mode == 0)
+                   ? cpm_launch_fused1<T>(c, A, (T)m, (T)n, (T)rowscale, cs, u, a, v, st)
+                   : 0;
+    if (launched == 0) {
+      launched = 1 + cpm_launch_gather1<T>(c, A, cs, u, a, st, diff);
+      cpm_launch_combine<T>(A, (T)m, (T)n, (T)rowscale, cs, u, a, v, nrhs, ld, st, diff);
+    }
   } else {
     cpm_launch_gather<T>(A, cs, u, a, nrhs, ld, st, diff);
     cpm_launch_combine<T>(A, (T)m, (T)n, (T)rowscale, cs, u, a, v, nrhs, ld, st, diff);

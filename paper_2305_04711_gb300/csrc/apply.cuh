@@ -66,6 +66,14 @@ int cpm_launch_gather1(const cpm_ctx *c, const ApplyArgs<T> &A, T cs, const T *u
 // precision and the columns per lane (1 or 2); the autotuner starts from it
 int cpm_cells_default_xh(int np1, bool fp64, int rpl);
 
+// the single right-hand side product in one persistent kernel (fused1.cu);
+// returns the launches (0: not built for this band)
+template <typename T>
+int cpm_launch_fused1(const cpm_ctx *c, const ApplyArgs<T> &A, T m, T n, T rowscale, T cs, const T *u, T *a, T *v,
+                      cudaStream_t st);
+cpm_status cpm_build_fused1(cpm_ctx *c);
+void cpm_free_fused1(cpm_ctx *c);
+
 cpm_status cpm_internal_extend(cpm_ctx *c, const double *u, double *a, int nrhs, int64_t ld, cudaStream_t st);
 cpm_status cpm_internal_rhs(cpm_ctx *c, const double *s, const double *g, const double *samples, double *f, int nrhs,
                             int64_t ld, cudaStream_t st);

@@ -519,6 +519,7 @@ __global__ void __launch_bounds__(256) correct1_kernel(const int32_t *__restrict
 }  // namespace
 
 void cpm_free_cells(cpm_ctx *c) {
+  cpm_free_fused1(c);
   cudaFree(c->d_cell_start); cudaFree(c->d_cell_rows); cudaFree(c->d_cell_key); cudaFree(c->d_nbr8);
   cudaFree(c->d_corr_row); cudaFree(c->d_corr_start); cudaFree(c->d_corr_node); cudaFree(c->d_corr_col);
   cudaFree(c->d_corr_w64); cudaFree(c->d_corr_w32); cudaFree(c->d_cell_lines); cudaFree(c->d_row_cell);
@@ -609,6 +610,7 @@ cpm_status cpm_build_cells(cpm_ctx *c) {
                                                               c->d_corr_col, c->d_corr_w64, c->d_corr_w32);
   TRY(cudaGetLastError());
   TRY(cudaStreamSynchronize(st));
+  rc = cpm_build_fused1(c);
 done:
 #undef TRY
   cudaFree(count); cudaFree(offs); cudaFree(flag); cudaFree(cellpos); cudaFree(d_tot);
@@ -703,7 +705,7 @@ int cpm_launch_gather1(const cpm_ctx *c, const ApplyArgs<T> &A, T cs, const T *u
   if (c->ncells == 0) return 0;
   const unsigned g = cpm_grid(c->NS, 256);
   const int2 *lines = reinterpret_cast<const int2 *>(c->d_cell_lines);
-  if (diff && c->tune.gather1_per_cell == 1) {
+  if (diff && c->tune.single_mode != 2) {
     // one thread per cell (the difference form only)
     const unsigned gc = cpm_grid(c->ncells, 128);
 #define CPM_G1C(D, NP)                                                                                           \

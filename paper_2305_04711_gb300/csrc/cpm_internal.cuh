@@ -33,6 +33,7 @@
 #define CPM_DEVERR_CP 2u             // a Newton closest point did not converge
 #define CPM_DEVERR_OVERLAP 4u        // a node lies within 2 r of two curves
 #define CPM_DEVERR_HASH 8u           // brick hash table full
+#define CPM_DEVERR_WAIT 16u          // a bounded wait of the fused product gave up
 
 struct CurveDev {
   int kind, bc, two_sided, n_samples;
@@ -78,7 +79,7 @@ struct Tune {
   int cells_blocks_per_sm = 0;            // grid cap of the cell gather (blocks of 8 warps per SM)
   int combine_warps_per_sm = 0;           // grid cap of the warp-per-row combine
   int vec_blocks_per_sm = 0;              // blocks per SM of the Krylov vector kernels (1, 2 or 4)
-  int gather1_per_cell = 0;               // single right-hand side gather: 1 thread per cell, 0 per row
+  int single_mode = 0;                    // single right-hand side: 0 fused, 1 per-cell / 2 per-row gather + combine
   bool tuned = false;
 };
 
@@ -169,6 +170,17 @@ struct cpm_ctx {
   int32_t *d_corr_col = nullptr;    // [ncorr_ent]
   double *d_corr_w64 = nullptr;     // [ncorr_ent]
   float *d_corr_w32 = nullptr;      // [ncorr_ent]
+  // single right-hand side fused product (fused1.cu): work items over z-slabs
+  int64_t f1_nitems = 0;
+  int f1_S = 0;
+  int2 *d_f1_items = nullptr;        // [f1_nitems] (kind << 28 | slab, first cell / brick / BC row)
+  int32_t *d_f1_gtot = nullptr;      // [S] gather items per slab
+  int32_t *d_f1_cend = nullptr;      // [S] end of each slab's cells
+  int32_t *d_f1_bend = nullptr;      // [S] end of each slab's bricks
+  unsigned *d_f1_sync = nullptr;     // [S + 2] gather items done per slab, ticket, exits
+  int32_t *d_f1_rows = nullptr;      // [NS] cell rows, bit 31 set where the row has flipped E entries
+  int32_t *d_corr_of_row = nullptr;  // [NS] index into the corr lists or -1
+  uint64_t *d_bspec = nullptr;       // [nb*8] rows near a curve, per brick
   // transposed structure (adjoint)
   bool transpose_ready = false;
   int64_t nT = 0;                   // entries of the per-column remainder lists

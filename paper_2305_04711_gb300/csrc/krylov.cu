@@ -433,27 +433,30 @@ __global__ void __launch_bounds__(KT, 2) init_kernel(Red R, Conv cv, int64_t N, 
 // r = f - r (r holds A x) and the weighted norms |W r|^2, |W f|^2 with W = wrow
 // on PDE rows and 1 on BC rows
 struct ResidBody {
-  const double *__restrict__ f; double *__restrict__ r; int64_t NS; double w2;
+  const double *__restrict__ f; double *__restrict__ r; int64_t NS; double w2, v2;
   struct Elt { double f, r; };
   __device__ bool on(int) const { return true; }
   __device__ void init(int) const {}
   __device__ void load(Elt &e, int64_t, int64_t o) const { e.f = f[o]; e.r = r[o]; }
-  __device__ void apply(Elt &e, int64_t i, int64_t o, double (&run)[2]) const {
+  __device__ void apply(Elt &e, int64_t i, int64_t o, double (&run)[3]) const {
     const double rv = e.f - e.r;
     r[o] = rv;
-    const double w = (i < NS) ? w2 : 1.0;
-    run[0] += w * (rv * rv);
-    run[1] += w * (e.f * e.f);
+    const bool pde = i < NS;
+    run[0] += (pde ? w2 : 1.0) * (rv * rv);
+    run[1] += (pde ? w2 : 1.0) * (e.f * e.f);
+    run[2] += (pde ? v2 : 1.0) * (rv * rv);
   }
 };
 
-__global__ void __launch_bounds__(KT, 2) resid_kernel(Red R, int64_t N, int64_t NS, double w2, int64_t ld,
+// r = f - r and, per column, |W r|^2, |W f|^2 (W = sqrt(w2) on PDE rows) and
+// |V r|^2 (V = sqrt(v2) on PDE rows; the norm of an iterated system)
+__global__ void __launch_bounds__(KT, 2) resid_kernel(Red R, int64_t N, int64_t NS, double w2, double v2, int64_t ld,
                                                    const double *f, double *r) {
-  ResidBody body{f, r, NS, w2};
-  double acc[2];
-  vloop<double, 2>(body, N, R.nrhs, ld, acc);
+  ResidBody body{f, r, NS, w2, v2};
+  double acc[3];
+  vloop<double, 3>(body, N, R.nrhs, ld, acc);
   Conv cv{0.0, 0.0, 0.0f, 0, 0u};
-  if (block_publish<2>(acc, R)) finish_reduce<2>(ST_OUT, R, cv);
+  if (block_publish<3>(acc, R)) finish_reduce<3>(ST_OUT, R, cv);
 }
 
 // y = x o xi with xi(i, c) = +-1 from a fixed hash: the model of the rounding
@@ -509,11 +512,13 @@ __global__ void ir_rhs_kernel(int64_t N, int64_t NS, double wrow, int nrhs, int6
   }
 }
 
-// x += d: the FP32 correction of an inner solve into the FP64 solution
-__global__ void ir_add_kernel(int64_t N, int nrhs, int64_t ld, const float *d32, double *x) {
+// x += s_c d: the FP32 correction of an inner solve into the FP64 solution
+// (s = nullptr: every column with s_c = 1; s_c = -1 takes a correction back)
+__global__ void ir_add_kernel(int64_t N, int nrhs, int64_t ld, const double *s, const float *d32, double *x) {
   CPM_ROWS_COLS_LOOP(N, nrhs, i, c) {
     int64_t o = i * ld + c;
-    x[o] += (double)d32[o];
+    const double sc = s ? s[c] : 1.0;
+    if (sc != 0.0) x[o] += sc * (double)d32[o];
   }
 }
 
@@ -768,16 +773,18 @@ cpm_status bicgstab(cpm_ctx *c, const Op<T> &op, const T *f, TX *x, bool x_zero,
 // |W r|^2 and |W f|^2 with W = diag(wrow on PDE rows, 1 on BC rows)
 cpm_status residual64(cpm_ctx *c, ApplyFn<double> fn, double m, double n, const double *f, const double *x,
                       SolveWork *w, int nrhs, int64_t ld, double wrow, std::vector<double> &rn2,
-                      std::vector<double> &fn2, cudaStream_t st) {
+                      std::vector<double> &fn2, cudaStream_t st, double vrow = 1.0,
+                      std::vector<double> *rv2 = nullptr) {
   const int64_t N = c->NS + c->NC;
   cpm_status rc = fn(c, m, n, 1.0, 1.0, x, w->r64, nrhs, ld, st);
   if (rc) return rc;
-  resid_kernel<<<(unsigned)w->G, KT, 0, st>>>(red_of(w, nrhs), N, c->NS, wrow * wrow, ld, f, w->r64);
+  resid_kernel<<<(unsigned)w->G, KT, 0, st>>>(red_of(w, nrhs), N, c->NS, wrow * wrow, vrow * vrow, ld, f, w->r64);
   cpm_count_launches(c, 1);
-  CPM_CUDA_TRY(cudaMemcpyAsync(w->h_pin, w->out, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaMemcpyAsync(w->h_pin, w->out, sizeof(double) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
   CPM_CUDA_TRY(cudaStreamSynchronize(st));
   rn2.assign(w->h_pin, w->h_pin + nrhs);
   fn2.assign(w->h_pin + nrhs, w->h_pin + 2 * nrhs);
+  if (rv2) rv2->assign(w->h_pin + 2 * nrhs, w->h_pin + 3 * nrhs);
   return CPM_OK;
 }
 
@@ -852,10 +859,14 @@ cpm_status ir_refine(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, do
   float *f32 = w->v32[5];  // first right-hand side: read by the init kernel before t is written
   const Conv cv{delta, 400.0, 0.0f, 1, 1u};
   const Red R = red_of(w, nrhs);
-  std::vector<double> flag(nrhs, 0.0), best(nrhs, INFINITY);
+  std::vector<double> flag(nrhs, 0.0), prev(nrhs, INFINITY);
   std::vector<int> stall(nrhs, 0);
   floors.assign(nrhs, 0.0);
-  cpm_status rc = residual64(c, ap64, m, n, f, x, w, nrhs, ld, wrow, rn2, fn2, st);
+  // the residual in the iterated system's norm (rhs_w on the PDE rows) decides
+  // whether a refinement step is kept: the plain norm may rise while the
+  // residual moves off the BC rows
+  std::vector<double> rv2, rv2_old;
+  cpm_status rc = residual64(c, ap64, m, n, f, x, w, nrhs, ld, wrow, rn2, fn2, st, rhs_w, &rv2);
   if (rc) return rc;
   int it_total = 0, nrep = 0, nrs = 0;
   while (true) {
@@ -868,8 +879,13 @@ cpm_status ir_refine(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, do
     for (int q = 0; q < nrhs; ++q) {
       flag[q] = 0.0;
       if (done_col(rn2[q], fn2[q], tol, floors[q])) continue;
-      if (rn2[q] < 0.25 * best[q]) { best[q] = rn2[q]; stall[q] = 0; }
-      else if (++stall[q] >= 3) continue;  // no gain over three replacements: FP64 finish
+      // a refinement that does not halve the residual is a stall (the first
+      // ones may raise the plain norm: the residual moves off the BC rows);
+      // three in a row leave the column to the FP64 finish
+      if (stall[q] >= 3) continue;
+      if (rn2[q] < 0.25 * prev[q]) stall[q] = 0;
+      else if (++stall[q] >= 3) continue;
+      prev[q] = rn2[q];
       flag[q] = 1.0;
       any = true;
     }
@@ -889,12 +905,33 @@ cpm_status ir_refine(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, do
     rc = krylov_run<float, float>(c, op32, w->d32, V, w, nrhs, ld, cv, maxit - it_total, check_every, &it, &rs,
                                   &broke, st);
     if (rc) return rc;
-    ir_add_kernel<<<g, 256, 0, st>>>(N, nrhs, ld, w->d32, x);
+    ir_add_kernel<<<g, 256, 0, st>>>(N, nrhs, ld, nullptr, w->d32, x);
     cpm_count_launches(c, 1);
     it_total += it;
     nrs += rs;
-    rc = residual64(c, ap64, m, n, f, x, w, nrhs, ld, wrow, rn2, fn2, st);
+    rv2_old = rv2;
+    rc = residual64(c, ap64, m, n, f, x, w, nrhs, ld, wrow, rn2, fn2, st, rhs_w, &rv2);
     if (rc) return rc;
+    // a step that raised its column's residual (an inner solve that drifted
+    // off the true residual) is taken back, and the column is left to the
+    // FP64 finish: repeating the same step would repeat the same drift
+    bool back = false;
+    for (int q = 0; q < nrhs; ++q) {
+      flag[q] = 0.0;
+      if (!(rv2[q] <= rv2_old[q])) {
+        flag[q] = -1.0;
+        stall[q] = 3;
+        back = true;
+      }
+    }
+    if (back) {
+      if (trace) std::fprintf(stderr, "[cpm ir] steps taken back after refinement %d\n", nrep);
+      CPM_CUDA_TRY(cudaMemcpyAsync(w->cols, flag.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+      ir_add_kernel<<<g, 256, 0, st>>>(N, nrhs, ld, w->cols, w->d32, x);
+      cpm_count_launches(c, 1);
+      rc = residual64(c, ap64, m, n, f, x, w, nrhs, ld, wrow, rn2, fn2, st, rhs_w, &rv2);
+      if (rc) return rc;
+    }
   }
   *iters = it_total;
   *nrepl_out = nrep;
@@ -905,7 +942,7 @@ cpm_status ir_refine(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, do
 // FP64 BiCGSTAB passes from the current x: the recursively updated residual
 // drifts from f - A x near the rounding level, so while the true residual is
 // above tol the iteration restarts from the current x, as long as a pass still
-// halves the worst true residual
+// lowers the worst true residual by 10 %
 cpm_status fp64_passes(cpm_ctx *c, ApplyFn<double> ap64, bool left, double dS, double m, double n, const double *f,
                        double *x, SolveWork *w, int nrhs, int64_t ld, double wrow, double tol, int maxit,
                        int check_every, int *iters, int *restarts, bool *broke, std::vector<double> &rn2,
@@ -913,9 +950,9 @@ cpm_status fp64_passes(cpm_ctx *c, ApplyFn<double> ap64, bool left, double dS, d
   const int64_t N = c->NS + c->NC;
   Vecs<double> V{w->v64[0], w->v64[1], w->v64[2], w->v64[3], w->v64[4], w->v64[5]};
   const Op<double> op = left ? Op<double>{ap64, m, n, dS, 1.0} : Op<double>{ap64, m, n, 1.0, dS};
-  const Conv cv{tol, 4000.0, 0.0f, 0, 0u};  // classical rhat = r (restarted on a first-step breakdown)
+  Conv cv{tol, 4000.0, 0.0f, 0, 0u};  // classical rhat = r (restarted on a first-step breakdown)
   double prev_worst = INFINITY;
-  for (int pass = 0; pass < 6; ++pass) {
+  for (int pass = 0; pass < 8; ++pass) {
     const double *rhs = f;
     if (left) {
       // W f into the t slot, which the initial residual reads before t is written
@@ -938,8 +975,16 @@ cpm_status fp64_passes(cpm_ctx *c, ApplyFn<double> ap64, bool left, double dS, d
       if (rc) return rc;
     }
     bool all = true;
-    for (int q = 0; q < nrhs; ++q) all = all && done_col(rn2[q], fn2[q], tol, floors[q]);
-    if (all || *broke || *iters >= maxit || !(worst < 0.5 * prev_worst)) break;
+    double fmin = INFINITY;
+    for (int q = 0; q < nrhs; ++q) {
+      const bool d = done_col(rn2[q], fn2[q], tol, floors[q]);
+      all = all && d;
+      if (!d) fmin = std::min(fmin, floors[q]);
+    }
+    // a further pass while the last one still gained 10 %; its recursion need
+    // not go below the rounding floor, where the true residual cannot follow
+    if (all || *broke || *iters >= maxit || !(worst < 0.9 * prev_worst)) break;
+    if (std::isfinite(fmin)) cv.tol = std::max(tol, 0.5 * fmin);
     prev_worst = worst;
   }
   return CPM_OK;
@@ -947,11 +992,11 @@ cpm_status fp64_passes(cpm_ctx *c, ApplyFn<double> ap64, bool left, double dS, d
 
 cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const double *f, double *x, int nrhs,
                       int64_t ld, const cpm_solve_opts *o, cpm_solve_stats *stats, cudaStream_t st) {
-  cpm_solve_opts opts{1e-10, 10000, CPM_SOLVE_FP64, 1e-2, 200, 16, CPM_NORM_PLAIN, 1000};
+  cpm_solve_opts opts{1e-10, 10000, CPM_SOLVE_FP64, 1e-1, 200, 16, CPM_NORM_PLAIN, 1000};
   if (o) opts = *o;
   if (opts.tol <= 0) opts.tol = 1e-10;
   if (opts.maxit <= 0) opts.maxit = 10000;
-  if (opts.inner_tol <= 0 || opts.inner_tol >= 1) opts.inner_tol = 1e-2;
+  if (opts.inner_tol <= 0 || opts.inner_tol >= 1) opts.inner_tol = 1e-1;
   if (opts.max_refine <= 0) opts.max_refine = 200;
   if (opts.check_every <= 0) opts.check_every = 16;
   if (opts.inner_maxit <= 0) opts.inner_maxit = 1000;

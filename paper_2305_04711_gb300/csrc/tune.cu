@@ -111,17 +111,17 @@ cpm_status tune_products(cpm_ctx *c, int nrhs, int64_t ld, T *u, T *v, cudaStrea
     info->cells_xh = t.cells_xh[pi][rpl - 1];
   }
   if (nrhs == 1 && c->ncells > 0) {
-    // the single right-hand side gather: a thread per row or per cell
-    int best_m = t.gather1_per_cell;
-    for (int mode : {0, 1}) {
-      t.gather1_per_cell = mode;
+    // the single right-hand side product: fused, or a gather per cell or per row then the combine
+    int best_m = t.single_mode;
+    for (int mode : {0, 1, 2}) {
+      t.single_mode = mode;
       double ms = 0.0;
       rc = time_products<T>(c, u, v, nrhs, ld, st, &ms);
       if (rc) return rc;
       if (ms < best) { best = ms; best_m = mode; }
     }
-    t.gather1_per_cell = best_m;
-    info->gather1_per_cell = best_m;
+    t.single_mode = best_m;
+    info->single_mode = best_m;
   }
   info->cells_blocks_per_sm = t.cells_blocks_per_sm;
   info->combine_warps_per_sm = t.combine_warps_per_sm;
@@ -139,13 +139,13 @@ cpm_status cpm_internal_set_tune(cpm_ctx *c, int nrhs, int prec, const cpm_tune_
   if (info->cells_blocks_per_sm < 0 || info->cells_blocks_per_sm > 256) return CPM_ERR_ARG;
   if (info->combine_warps_per_sm < 0 || info->combine_warps_per_sm > 256) return CPM_ERR_ARG;
   if (info->vec_blocks_per_sm < 0 || info->vec_blocks_per_sm > 4 || info->vec_blocks_per_sm == 3) return CPM_ERR_ARG;
-  if (info->gather1_per_cell != 0 && info->gather1_per_cell != 1) return CPM_ERR_ARG;
+  if (info->single_mode < 0 || info->single_mode > 2) return CPM_ERR_ARG;
   const int rpl = cells_rpl(nrhs, nrhs);
   if (rpl > 0) c->tune.cells_xh[fp64 ? 1 : 0][rpl - 1] = xh;
   c->tune.cells_blocks_per_sm = info->cells_blocks_per_sm;
   c->tune.combine_warps_per_sm = info->combine_warps_per_sm;
   c->tune.vec_blocks_per_sm = info->vec_blocks_per_sm;
-  c->tune.gather1_per_cell = info->gather1_per_cell;
+  c->tune.single_mode = info->single_mode;
   return CPM_OK;
 }
 

@@ -261,8 +261,8 @@ def test_every_launch_shape_keeps_the_products(oracle_mod, torch_mod, p):
                         else:
                             assert np.max(np.abs(V - VR[:, :nrhs])) <= 2e-6 * np.max(np.abs(VR)), (nrhs, xh, g, wps)
         u1 = torch.tensor(U[:, 0], device="cuda", dtype=dt).contiguous()
-        for mode in (0, 1):
-            band.set_tune(1, dt, gather1_per_cell=mode)
+        for mode in (0, 1, 2):
+            band.set_tune(1, dt, single_mode=mode)
             v = band.apply(0.0, 1.0, u1).cpu().numpy()
             if dt == torch.float64:
                 assert rel_inf(v, VR[:, 0]) < 1e-14, mode
