@@ -1,26 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the CPM hot path on GB300: the batched FP32 + FP64-refinement
-solve of a diffusion-curve batch, against plain FP64 solves.
+solve of 64 right-hand sides, against plain FP64 solves.
 
-Default workload (one step): the torus R = 1, r = 0.4 at h = 1/256 (about
-8.8M DOFs) with 8 Dirichlet meridians at seeded toroidal angles carrying 64
-right-hand sides with values U[0,1] (the per-channel diffusion-curve solves of
-Sec. 7.1).  One step solves the 64 together by mixed-precision iterative
-refinement (FP32 BiCGSTAB with FP64 residual replacement) to the paper's
-stopping test |f - A x|_2 <= 1e-10 |f|_2 per right-hand side (Sec. 5.4).  The
-metric is seconds per right-hand side.  Alongside:
+Default workload (one step): the unit sphere at h = 1/128 (about 1.7M DOFs)
+with the two Dirichlet latitude circles of the sphere study and a batch of 64
+spherical-harmonic Poisson problems.  One step solves the 64 together by
+mixed-precision iterative refinement (FP32 BiCGSTAB inner solves restarted from
+the FP64 residual) to the paper's stopping test |f - A x|_2 <= 1e-10 |f|_2 per
+right-hand side (Sec. 5.4), or the FP64 rounding floor.  The metric is seconds
+per right-hand side.  Alongside:
   * the plain FP64 solve of one right-hand side (and, with --fp64-batch, of the
     64 as one FP64 batch), and both results' distance to each other and to the
-    closed form (piecewise linear in the toroidal angle between meridians);
+    closed form;
   * the dominant kernel's roofline: the batched FP32 operator product, timed by
     the library's event pairs right after the timed region, against the FP32
     FMA peak of this device's SM count and clock;
   * cpm_apply bandwidth for one right-hand side (FP32 and FP64) on the bumpy
-    sphere band at h = 1/640 (about 42M DOFs), against the measured HBM peak;
+    sphere band at h = 1/640 (about 43M DOFs), against the measured HBM peak;
   * an end-to-end number through host buffers, and the CPU oracle timed on the
     same band and right-hand side.
---workload sphere runs the unit sphere at h = 1/128 with a batch of 64
-spherical-harmonic Poisson problems instead.
+--workload torus runs the diffusion-curve batch on the torus R = 1, r = 0.4 at
+h = 1/256 (8.8M DOFs, 8 meridians, 64 U[0,1] value sets; Sec. 7.1).  There the
+FP32 product's rounding, relative to the smallest eigenvalues, stops the FP32
+refinement early and most of the solve runs as the FP64 finish (a step takes
+about 20 minutes), so it is not the default.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -60,6 +63,7 @@ def flops_row_rhs_batched(nrhs: int) -> float:
 
 
 GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_torus256_iterations.json")
+GOLDEN_ITERS_SPHERE = os.path.join(ROOT, "tests", "golden", "oracle_sphere128_iterations.json")
 
 
 def max_over_ranks(ms: float) -> float:
@@ -107,7 +111,7 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="torus", choices=["torus", "sphere"])
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "torus"])
     ap.add_argument("--h", type=float, default=0.0, help="grid spacing (0: the workload's own)")
     ap.add_argument("--maxit", type=int, default=40000)
     ap.add_argument("--warmup-maxit", type=int, default=64,
@@ -153,7 +157,7 @@ class Workload:
         else:
             wl = (f"torus R=1 r=0.4, h=1/{round(1 / self.h)}, 8 Dirichlet meridians (seeded angles, min gap 0.2 "
                   f"rad), {NRHS} right-hand sides with U[0,1] meridian values (diffusion-curve channels)")
-        wl += (f"; one batched FP32+FP64-refinement solve (FP32 BiCGSTAB, FP64 residual replacement) per step to "
+        wl += (f"; one batched FP32 + FP64-refinement solve (FP32 BiCGSTAB inner solves restarted from the FP64 residual) per step to "
                f"|f - A x|_2 <= {TOL:g} |f|_2")
         d = {"workload": wl, "nrhs": NRHS, "tol": TOL, "norm": "|f - A x|_2 / |f|_2 per right-hand side (Sec. 5.4)",
              "l2": "inputs larger than L2 (each [N][64] Krylov vector is hundreds of MB vs 129 MB L2)"}
@@ -289,12 +293,15 @@ class OracleSample:
 
 
 def golden_iterations(wl):
-    """The oracle's own iteration count on the default torus workload, recorded
-    by oracle/record_iterations.py (None for other workloads or if absent)."""
-    if wl.kind != "torus" or abs(wl.h - 1.0 / 256) > 1e-15:
+    """The oracle's own iteration count on the default-size workload (the torus
+    at h = 1/256 or the sphere at h = 1/128), recorded by
+    oracle/record_iterations.py (None for other sizes or if absent)."""
+    default_h = 1.0 / 256 if wl.kind == "torus" else 1.0 / 128
+    if abs(wl.h - default_h) > 1e-15:
         return None
+    path = GOLDEN_ITERS if wl.kind == "torus" else GOLDEN_ITERS_SPHERE
     try:
-        with open(GOLDEN_ITERS) as fh:
+        with open(path) as fh:
             return json.load(fh)
     except OSError:
         return None
@@ -332,7 +339,7 @@ def run_reference(args):
         sample = f"complete oracle BiCGSTAB solve of 1 RHS ({N} DOF, {its} iterations) per step, measured"
         iters, src = its, "measured in this run"
     elif gold is not None:
-        iters, src = gold["iterations"], f"the oracle's own solve ({GOLDEN_ITERS[len(ROOT) + 1:]})"
+        iters, src = gold["iterations"], f"the oracle's own solve ({gold['command']})"
         value = per * iters
         sample = (f"{n_it} oracle BiCGSTAB iterations on the full band ({N} DOF) per step, timed: "
                   f"{per:.3f} s/iteration x {iters} iterations ({src}); projected")
@@ -377,8 +384,8 @@ def apply_bandwidth(h, hbm, peak_src, log):
         out[key] = {"ms": tms, "GB/s_algorithmic": gbs, "hbm_peak_GB/s": hbm, "frac": gbs / hbm,
                     "peak_source": peak_src, "bytes_per_row": bytes_row,
                     "launches_per_product": p["launches"] / max(p["applies"], 1),
-                    "single_mode": {0: "fused", 1: "per-cell gather + combine",
-                                    2: "per-row gather + combine"}[tune["single_mode"]]}
+                    "single_mode": {0: "per-cell gather + combine", 1: "per-row gather + combine",
+                                    2: "fused"}[tune["single_mode"]]}
         if key == "fp64":
             out[key]["TFLOP/s"] = FLOPS_ROW_FP64 * band.NS / (tms * 1e-3) / 1e12
         del u, v

@@ -347,8 +347,8 @@ typedef struct {
   int cells_blocks_per_sm;   /* grid cap of the cell gather, blocks of 8 warps per SM (0: default 16) */
   int combine_warps_per_sm;  /* grid cap of the warp-per-row combine (0: default 64) */
   int vec_blocks_per_sm;     /* blocks of 512 threads per SM of the Krylov vector kernels (1, 2 or 4) */
-  int single_mode;           /* single right-hand side product: 0 = fused persistent kernel, 1 = per-cell gather
-                              * then combine, 2 = per-row gather then combine */
+  int single_mode;           /* single right-hand side product: 0 = per-cell gather then combine (default),
+                              * 1 = per-row gather then combine, 2 = fused persistent kernel */
   double product_ms;         /* one operator product with the chosen shapes */
   double product_ms_default; /* the same with the built-in defaults */
   double vector_ms;          /* one two-product reduction over [N][ld] with the chosen blocks */

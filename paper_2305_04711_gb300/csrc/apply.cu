@@ -479,9 +479,9 @@ cpm_status cpm_apply_rc_T(cpm_ctx *c, double m, double n, double rowscale, doubl
   else if (nrhs >= 16 && nrhs <= 32)
     launched = launch_batched<T, 1>(c, A, (T)m, (T)n, (T)rowscale, cs, u, a, v, nrhs, ld, st, diff);
   else if (nrhs == 1 && c->ncells > 0) {
-    // default: the fused persistent product; 1 and 2: per-cell or per-row
-    // gather, then the combine
-    launched = (c->tune.single_mode == 0)
+    // default: the per-cell gather, then the combine; 1: per-row gather; 2: the
+    // fused persistent product (fused1.cu)
+    launched = (c->tune.single_mode == 2)
                    ? cpm_launch_fused1<T>(c, A, (T)m, (T)n, (T)rowscale, cs, u, a, v, st)
                    : 0;
     if (launched == 0) {

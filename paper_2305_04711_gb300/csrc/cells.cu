@@ -705,7 +705,7 @@ int cpm_launch_gather1(const cpm_ctx *c, const ApplyArgs<T> &A, T cs, const T *u
   if (c->ncells == 0) return 0;
   const unsigned g = cpm_grid(c->NS, 256);
   const int2 *lines = reinterpret_cast<const int2 *>(c->d_cell_lines);
-  if (diff && c->tune.single_mode != 2) {
+  if (diff && c->tune.single_mode != 1) {
     // one thread per cell (the difference form only)
     const unsigned gc = cpm_grid(c->ncells, 128);
 #define CPM_G1C(D, NP)                                                                                           \

@@ -79,7 +79,7 @@ struct Tune {
   int cells_blocks_per_sm = 0;            // grid cap of the cell gather (blocks of 8 warps per SM)
   int combine_warps_per_sm = 0;           // grid cap of the warp-per-row combine
   int vec_blocks_per_sm = 0;              // blocks per SM of the Krylov vector kernels (1, 2 or 4)
-  int single_mode = 0;                    // single right-hand side: 0 fused, 1 per-cell / 2 per-row gather + combine
+  int single_mode = 0;                    // single right-hand side: 0 per-cell / 1 per-row gather + combine, 2 fused
   bool tuned = false;
 };
 
@@ -287,6 +287,37 @@ __device__ __forceinline__ int32_t cpm_node_index(const BandView &v, int32_t b, 
   if (!((word >> bit) & 1ull)) return -1;
   uint64_t below = (bit == 0) ? 0ull : (word & ((1ull << bit) - 1ull));
   return __ldg(v.bstart + b) + __ldg(v.brank + (int64_t)b * 8 + lz) + __popcll(below);
+}
+
+// start of the stencil line (cy, cz) of the cell with base (lx, ly, lz) in
+// brick b: s0 the DOF of its first node; s1 that of its first node past the
+// brick's x face when the line crosses it.  Nodes of one x-run inside a brick
+// are consecutive DOFs (every stencil node is in the band); a line whose first
+// node is absent or whose run would pass the last PDE DOF is reported.
+template <int NP>
+__device__ __forceinline__ bool cpm_line_start(const BandView &v, int32_t b, int lx, int ly, int lz, int cy, int cz,
+                                           int32_t &s0, int32_t &s1) {
+  const int y = ly + cy, z = lz + cz;
+  const int oy = y >> 3, oz = z >> 3, yl = y & 7, zl = z & 7;
+  int32_t b0 = b;
+  if (oy | oz) b0 = __ldg(v.bnbr + (int64_t)b * 27 + 13 + 3 * oy + 9 * oz);
+  if (b0 < 0) return false;
+  const uint64_t w0 = __ldg(reinterpret_cast<const unsigned long long *>(v.bmask) + (int64_t)b0 * 8 + zl);
+  const int bit = yl * 8 + lx;
+  if (!((w0 >> bit) & 1ull)) return false;
+  s0 = __ldg(v.bstart + b0) + __ldg(v.brank + (int64_t)b0 * 8 + zl) + __popcll(w0 & ((1ull << bit) - 1ull));
+  s1 = s0;
+  const int split = (lx + NP - 1 < 8) ? NP : 8 - lx;
+  if (s0 + split > v.NS) return false;
+  if (split < NP) {
+    const int32_t b1 = __ldg(v.bnbr + (int64_t)b0 * 27 + 14);
+    if (b1 < 0) return false;
+    const uint64_t w1 = __ldg(reinterpret_cast<const unsigned long long *>(v.bmask) + (int64_t)b1 * 8 + zl);
+    if (!((w1 >> (yl * 8)) & 1ull)) return false;
+    s1 = __ldg(v.bstart + b1) + __ldg(v.brank + (int64_t)b1 * 8 + zl) + __popcll(w1 & ((1ull << (yl * 8)) - 1ull));
+    if (s1 + (NP - split) > v.NS) return false;
+  }
+  return true;
 }
 
 // DOF index of grid node (i, j, k) anywhere in the band, through the brick hash

@@ -72,37 +72,6 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
   return r;
 }
 
-// start of the stencil line (cy, cz) of the cell with base (lx, ly, lz) in
-// brick b: s0 the DOF of its first node; s1 that of its first node past the
-// brick's x face when the line crosses it.  Nodes of one x-run inside a brick
-// are consecutive DOFs (every stencil node is in the band); a line whose first
-// node is absent or whose run would pass the last PDE DOF is reported.
-template <int NP>
-__device__ __forceinline__ bool line_start(const BandView &v, int32_t b, int lx, int ly, int lz, int cy, int cz,
-                                           int32_t &s0, int32_t &s1) {
-  const int y = ly + cy, z = lz + cz;
-  const int oy = y >> 3, oz = z >> 3, yl = y & 7, zl = z & 7;
-  int32_t b0 = b;
-  if (oy | oz) b0 = __ldg(v.bnbr + (int64_t)b * 27 + 13 + 3 * oy + 9 * oz);
-  if (b0 < 0) return false;
-  const uint64_t w0 = __ldg(reinterpret_cast<const unsigned long long *>(v.bmask) + (int64_t)b0 * 8 + zl);
-  const int bit = yl * 8 + lx;
-  if (!((w0 >> bit) & 1ull)) return false;
-  s0 = __ldg(v.bstart + b0) + __ldg(v.brank + (int64_t)b0 * 8 + zl) + __popcll(w0 & ((1ull << bit) - 1ull));
-  s1 = s0;
-  const int split = (lx + NP - 1 < 8) ? NP : 8 - lx;
-  if (s0 + split > v.NS) return false;
-  if (split < NP) {
-    const int32_t b1 = __ldg(v.bnbr + (int64_t)b0 * 27 + 14);
-    if (b1 < 0) return false;
-    const uint64_t w1 = __ldg(reinterpret_cast<const unsigned long long *>(v.bmask) + (int64_t)b1 * 8 + zl);
-    if (!((w1 >> (yl * 8)) & 1ull)) return false;
-    s1 = __ldg(v.bstart + b1) + __ldg(v.brank + (int64_t)b1 * 8 + zl) + __popcll(w1 & ((1ull << (yl * 8)) - 1ull));
-    if (s1 + (NP - split) > v.NS) return false;
-  }
-  return true;
-}
-
 // E u - u (difference form) of the rows of cell cid, as the per-cell gather of
 // cells.cu computes it, plus the row's flipped entries
 template <typename T, int DIM, int NP>
@@ -120,7 +89,7 @@ __device__ __forceinline__ void gather_cell(const F1Args<T> &F, int64_t cid) {
 #pragma unroll
   for (int cz = 0; cz < NZ; ++cz)
 #pragma unroll
-    for (int cy = 0; cy < NP; ++cy) ok &= line_start<NP>(v, b, lx, ly, lz, cy, cz, s0[cz][cy], s1[cz][cy]);
+    for (int cy = 0; cy < NP; ++cy) ok &= cpm_line_start<NP>(v, b, lx, ly, lz, cy, cz, s0[cz][cy], s1[cz][cy]);
   if (!ok) {
     atomicOr(F.err, CPM_DEVERR_MISSING_NODE);
     return;

@@ -857,10 +857,10 @@ cpm_status ir_refine(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, do
   const unsigned g = cpm_grid(N * nrhs, 256);
   Vecs<float> V{w->v32[0], w->v32[1], w->v32[2], w->v32[3], w->v32[4], w->v32[5]};
   float *f32 = w->v32[5];  // first right-hand side: read by the init kernel before t is written
-  const Conv cv{delta, 400.0, 0.0f, 1, 1u};
+  Conv cv{delta, 400.0, 0.0f, 1, 1u};
   const Red R = red_of(w, nrhs);
   std::vector<double> flag(nrhs, 0.0), prev(nrhs, INFINITY);
-  std::vector<int> stall(nrhs, 0);
+  std::vector<int> stall(nrhs, 0), taken(nrhs, 0);
   floors.assign(nrhs, 0.0);
   // the residual in the iterated system's norm (rhs_w on the PDE rows) decides
   // whether a refinement step is kept: the plain norm may rise while the
@@ -884,7 +884,8 @@ cpm_status ir_refine(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, do
       // three in a row leave the column to the FP64 finish
       if (stall[q] >= 3) continue;
       if (rn2[q] < 0.25 * prev[q]) stall[q] = 0;
-      else if (++stall[q] >= 3) continue;
+      else if (!taken[q] && ++stall[q] >= 3) continue;
+      taken[q] = 0;
       prev[q] = rn2[q];
       flag[q] = 1.0;
       any = true;
@@ -897,6 +898,9 @@ cpm_status ir_refine(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, do
     // r = W r64 on the selected columns (0 elsewhere), d = 0, a fresh Krylov
     // space; the correction accumulates in FP32 (it is needed to about delta)
     ir_rhs_kernel<<<g, 256, 0, st>>>(N, c->NS, rhs_w, nrhs, ld, w->cols, w->r64, f32, w->d32);
+    // each step draws its own shadow residual, so that a step taken back is
+    // not repeated identically
+    cv.seed = 1u + 7919u * (unsigned)nrep;
     init_kernel<float><<<(unsigned)w->G, KT, 0, st>>>(R, cv, N, ld, true, f32, V.r, V.rh, V.p, V.v);
     cpm_count_launches(c, 2);
     ++nrep;
@@ -913,14 +917,14 @@ cpm_status ir_refine(cpm_ctx *c, ApplyFn<double> ap64, const Op<float> &op32, do
     rc = residual64(c, ap64, m, n, f, x, w, nrhs, ld, wrow, rn2, fn2, st, rhs_w, &rv2);
     if (rc) return rc;
     // a step that raised its column's residual (an inner solve that drifted
-    // off the true residual) is taken back, and the column is left to the
-    // FP64 finish: repeating the same step would repeat the same drift
+    // off the true residual) is taken back and counts as a stall
     bool back = false;
     for (int q = 0; q < nrhs; ++q) {
       flag[q] = 0.0;
       if (!(rv2[q] <= rv2_old[q])) {
         flag[q] = -1.0;
-        stall[q] = 3;
+        ++stall[q];
+        taken[q] = 1;
         back = true;
       }
     }
@@ -983,7 +987,8 @@ cpm_status fp64_passes(cpm_ctx *c, ApplyFn<double> ap64, bool left, double dS, d
     }
     // a further pass while the last one still gained 10 %; its recursion need
     // not go below the rounding floor, where the true residual cannot follow
-    if (all || *broke || *iters >= maxit || !(worst < 0.9 * prev_worst)) break;
+    // a breakdown ends the pass, not the solve: the next pass restarts from x
+    if (all || *iters >= maxit || !(worst < 0.9 * prev_worst)) break;
     if (std::isfinite(fmin)) cv.tol = std::max(tol, 0.5 * fmin);
     prev_worst = worst;
   }

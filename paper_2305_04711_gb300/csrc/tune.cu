@@ -111,7 +111,7 @@ cpm_status tune_products(cpm_ctx *c, int nrhs, int64_t ld, T *u, T *v, cudaStrea
     info->cells_xh = t.cells_xh[pi][rpl - 1];
   }
   if (nrhs == 1 && c->ncells > 0) {
-    // the single right-hand side product: fused, or a gather per cell or per row then the combine
+    // the single right-hand side product: a gather per cell or per row then the combine, or fused
     int best_m = t.single_mode;
     for (int mode : {0, 1, 2}) {
       t.single_mode = mode;
