@@ -55,6 +55,7 @@ class Curve:
     ref: Sequence[float] = (1.0, 0.0, 0.0)
     two_sided: bool = False
     bc_minus: int = 0        # BC type on the minus side (0: the same as bc, the plus side's)
+    projected: bool = False  # the projected crossing test (Sec. 4.7) instead of the plain one
 
 
 @dataclasses.dataclass

@@ -72,6 +72,7 @@ typedef struct {
   double ref[3];     /* circle: unit reference direction in its plane (angle 0) */
   int two_sided;     /* 0: one value set for both sides; 1: separate sets per side */
   int bc_minus;      /* BC type on the minus side (0: the same as bc, which is the plus side's) */
+  int projected;     /* 1: projected crossing test of Sec. 4.7 (components along n_S and t_C removed) */
 } orc_curve;
 
 /* ------------------------------------------------------------------ */
@@ -545,12 +546,59 @@ static void stencil_of(const orc_ctx *c, const double *y, int base[3], double t[
  * short, i.e. that node's vector stands in for its own.  (An exactly-zero
  * vector that flipped nothing would leave the rows of nodes on S_perp as plain
  * Laplacian rows across C, and the IBC would not be imposed there.) */
+/* Unit normal of S at a point y on S (Sec. 4.7 evaluates it at cp_C(x)):
+ * circle and sphere y/|y|; torus (y - ring point)/|...|; bumpy sphere
+ * grad phi/|grad phi| (App. A).  Reading: the analytic shapes give the normal in
+ * closed form, where the paper (for meshes) takes the eigenvector of the FD
+ * Jacobian of cp_S; both are the normal of S at that point. */
+static void shape_normal(const orc_shape *sh, const double *y, double n[3]) {
+  if (sh->kind == SH_BUMPY) {
+    double phi, g[3], hs[9];
+    bumpy_phi(sh, y, &phi, g, hs);
+    double m = sqrt((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]);
+    n[0] = g[0] / m; n[1] = g[1] / m; n[2] = g[2] / m;
+    return;
+  }
+  double d[3] = {y[0], y[1], y[2]};
+  if (sh->kind == SH_CIRCLE) d[2] = 0.0;
+  if (sh->kind == SH_TORUS) {
+    double rho = sqrt(y[0] * y[0] + y[1] * y[1]);
+    d[0] = y[0] - sh->R * (y[0] / rho);
+    d[1] = y[1] - sh->R * (y[1] / rho);
+  }
+  double m = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+  n[0] = d[0] / m; n[1] = d[1] / m; n[2] = d[2] / m;
+}
+
+/* Unit tangent of a circle C at its point cc: nu x (cc - p), normalised */
+static void circle_tangent(const orc_curve *cv, const double *cc, double t[3]) {
+  double w[3] = {cc[0] - cv->p[0], cc[1] - cv->p[1], cc[2] - cv->p[2]};
+  double u[3] = {cv->nu[1] * w[2] - cv->nu[2] * w[1], cv->nu[2] * w[0] - cv->nu[0] * w[2],
+                 cv->nu[0] * w[1] - cv->nu[1] * w[0]};
+  double m = sqrt((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2]);
+  t[0] = u[0] / m; t[1] = u[1] / m; t[2] = u[2] / m;
+}
+
+/* cp_{S-C}(x) of one node; with the projected test (Sec. 4.7, Eq. for
+ * cp-perp) the components along n_S and t_C at cp_C(x) are removed, in that
+ * order (a point C has no tangent: n_S only) */
 static void cpdiff_raw(const orc_ctx *c, const orc_curve *cv, int64_t node, double z[3]) {
   double x[3], cc[3];
   node_x(c, c->ijk + 3 * node, x);
   cp_C(cv, x, cc);
   const double *cs = c->cp + 3 * node;
   z[0] = cs[0] - cc[0]; z[1] = cs[1] - cc[1]; z[2] = cs[2] - cc[2];
+  if (!cv->projected) return;
+  double n[3];
+  shape_normal(&c->sh, cc, n);
+  double a = dot3(z, n);
+  z[0] = z[0] - a * n[0]; z[1] = z[1] - a * n[1]; z[2] = z[2] - a * n[2];
+  if (cv->kind == CV_CIRCLE) {
+    double t[3];
+    circle_tangent(cv, cc, t);
+    double b = dot3(z, t);
+    z[0] = z[0] - b * t[0]; z[1] = z[1] - b * t[1]; z[2] = z[2] - b * t[2];
+  }
 }
 static void cpdiff(const orc_ctx *c, const orc_curve *cv, int64_t node, double z[3]) {
   double tiny = 0.1 * c->h * c->h;
@@ -658,6 +706,13 @@ void orc_export_bc(const orc_ctx *c, int64_t *twin, int32_t *curve, double *cpc,
   if (cpc) memcpy(cpc, c->cpc, sizeof(double) * 3 * c->NC);
   if (side) memcpy(side, c->bc_side, sizeof(int32_t) * c->NC);
   if (type) memcpy(type, c->bc_type, sizeof(int32_t) * c->NC);
+}
+/* the (tie-resolved, possibly projected) crossing vector cp_{S-C} of PDE
+ * node i for curve k, as the crossing test uses it */
+int orc_crossing_vector(const orc_ctx *c, int k, int64_t i, double *z) {
+  if (!c || k < 0 || k >= c->ncurves || i < 0 || i >= c->NS) return ORC_ERR_ARG;
+  cpdiff(c, &c->curves[k], i, z);
+  return 0;
 }
 void orc_export_near(const orc_ctx *c, int32_t *near_c, int64_t *bc_of) {
   if (near_c) memcpy(near_c, c->near_c, sizeof(int32_t) * c->NS);

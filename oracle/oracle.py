@@ -55,7 +55,7 @@ class _Shape(ctypes.Structure):
 class _Curve(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("bc", ctypes.c_int), ("p", ctypes.c_double * 3),
                 ("nu", ctypes.c_double * 3), ("rad", ctypes.c_double), ("ref", ctypes.c_double * 3),
-                ("two_sided", ctypes.c_int), ("bc_minus", ctypes.c_int)]
+                ("two_sided", ctypes.c_int), ("bc_minus", ctypes.c_int), ("projected", ctypes.c_int)]
 
 
 _lib = None
@@ -90,6 +90,7 @@ def lib():
         L.orc_cp.argtypes = [ctypes.POINTER(_Shape), P, P]
         L.orc_bumpy_phi.argtypes = [ctypes.POINTER(_Shape), P, P, P, P]
         L.orc_cpc.argtypes = [ctypes.POINTER(_Curve), P, P]
+        L.orc_crossing_vector.argtypes = [P, i32, i64, P]
         L.orc_bary_weights.argtypes = [i32, d, P]
         L.orc_num_threads.restype = i32
         _lib = L
@@ -127,6 +128,7 @@ def make_curves(curves: Sequence[ci.Curve]):
         c.rad = cv.rad
         c.two_sided = int(cv.two_sided)
         c.bc_minus = int(getattr(cv, "bc_minus", 0) or 0)
+        c.projected = int(bool(getattr(cv, "projected", False)))
     return arr
 
 
@@ -399,6 +401,13 @@ class Oracle:
         d = np.ones(self.N)
         d[:self.NS] = 1.0 / (m + n * self.diagL())
         return d
+
+    def crossing_vector(self, k: int, i: int) -> np.ndarray:
+        """The crossing vector cp_{S-C}(x_i) for curve k as the crossing test uses
+        it (tie-resolved; projected when the curve asks for Sec. 4.7's test)."""
+        z = np.zeros(3)
+        _check(lib().orc_crossing_vector(self._h, int(k), int(i), _ptr(z)))
+        return z
 
     def solve_direct(self, m: float, n: float, f: np.ndarray) -> np.ndarray:
         lu = spla.splu(self.A(m, n).tocsc())
