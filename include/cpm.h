@@ -103,7 +103,10 @@ typedef struct {
  *   NEU1  u_alpha - sum w u       = 0       (stencil at cp_C(x_alpha))
  *   NEU2  u_alpha - sum wbar u    = 0       (stencil at cpbar_C)
  * where a stencil node keeps its BC twin unless the crossing test puts it on
- * the other side (Eq. 11).  Neumann types need sides: not for points in 3D. */
+ * the other side (Eq. 11).  Neumann types need sides: not for points in 3D.
+ * With `projected` the normal and tangent come in closed form from the shape
+ * (sphere, circle, torus: the radial directions; bumpy sphere: the level-set
+ * gradient) and the circle (nu x (cp_C - p)). */
 typedef struct {
   int kind;       /* cpm_curve_kind */
   int bc;         /* cpm_bc_kind on the plus side (and on both when bc_minus = 0) */
@@ -114,6 +117,11 @@ typedef struct {
   int two_sided;  /* 0: one sample set for both sides; 1: plus-side then minus-side sets */
   int n_samples;  /* >= 1 */
   int bc_minus;   /* cpm_bc_kind on the minus side, or 0 for the same as bc */
+  int projected;  /* 1: the projected crossing test of Sec. 4.7 -- before the sign test of
+                     Eq. (9) the vectors cp_{S-C} lose their components along the surface
+                     normal n_S and the curve tangent t_C, both at cp_C(x) (a point: n_S
+                     only), which keeps the test reliable where S bends strongly near C;
+                     0: the plain test of Eq. (9) */
 } cpm_curve_desc;
 
 typedef enum { CPM_NORM_PLAIN = 0, CPM_NORM_SCALED = 1 } cpm_norm;

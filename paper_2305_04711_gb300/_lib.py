@@ -38,7 +38,8 @@ class ShapeDesc(ctypes.Structure):
 class CurveDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("bc", ctypes.c_int), ("p", ctypes.c_double * 3),
                 ("nu", ctypes.c_double * 3), ("rad", ctypes.c_double), ("ref", ctypes.c_double * 3),
-                ("two_sided", ctypes.c_int), ("n_samples", ctypes.c_int), ("bc_minus", ctypes.c_int)]
+                ("two_sided", ctypes.c_int), ("n_samples", ctypes.c_int), ("bc_minus", ctypes.c_int),
+                ("projected", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):

@@ -87,6 +87,7 @@ def curve_descs(curves: Sequence, n_samples: Optional[Sequence[int]] = None):
         c.two_sided = int(bool(getattr(cv, "two_sided", False)))
         c.n_samples = int(n_samples[i]) if n_samples is not None else 1
         c.bc_minus = int(getattr(cv, "bc_minus", 0) or 0)
+        c.projected = int(bool(getattr(cv, "projected", False)))
     return arr
 
 

@@ -57,6 +57,28 @@ __device__ __forceinline__ int32_t lookup_near(const BView &b, int32_t j, int gi
   return cpm_node_index(b.v, bj, lx, ly, lz);
 }
 
+// unit normal of S at a point y on S: the radial direction of the circle and
+// the sphere, the direction from the torus's ring, the level-set gradient of
+// the bumpy sphere (App. A)
+__device__ void shape_normal(const ShapeDev &sh, const double *y, double n[3]) {
+  double d[3] = {y[0], y[1], y[2]};
+  if (sh.kind == CPM_SHAPE_BUMPY) {
+    double phi;
+    cpm_bumpy::bumpy_eval(sh, y, &phi, d, nullptr);
+  } else if (sh.kind == CPM_SHAPE_CIRCLE) {
+    d[2] = 0.0;
+  } else if (sh.kind == CPM_SHAPE_TORUS) {
+    const double rho = rn_sqrt(rn_add(rn_mul(y[0], y[0]), rn_mul(y[1], y[1])));
+    d[0] = rn_sub(y[0], rn_mul(sh.R, rn_div(y[0], rho)));
+    d[1] = rn_sub(y[1], rn_mul(sh.R, rn_div(y[1], rho)));
+  }
+  const double m = rn_norm3(d);
+  n[0] = rn_div(d[0], m); n[1] = rn_div(d[1], m); n[2] = rn_div(d[2], m);
+}
+
+// cp_{S-C}(x_j); with the projected test (Sec. 4.7) its components along n_S
+// and the circle's tangent nu x (cp_C - p), both at cp_C(x_j), removed in that
+// order (a point: n_S only)
 __device__ __forceinline__ void zraw(const BView &b, const CurveDev &cv, int32_t j, double z[3]) {
   double x[3], cc[3];
   node_coords(b, j, x);
@@ -64,6 +86,21 @@ __device__ __forceinline__ void zraw(const BView &b, const CurveDev &cv, int32_t
   z[0] = rn_sub(b.cp[3 * j], cc[0]);
   z[1] = rn_sub(b.cp[3 * j + 1], cc[1]);
   z[2] = rn_sub(b.cp[3 * j + 2], cc[2]);
+  if (!cv.projected) return;
+  double n[3];
+  shape_normal(b.shape, cc, n);
+  const double a = rn_dot3(z, n);
+  for (int e = 0; e < 3; ++e) z[e] = rn_sub(z[e], rn_mul(a, n[e]));
+  if (cv.kind == CPM_CURVE_CIRCLE) {
+    const double w[3] = {rn_sub(cc[0], cv.p[0]), rn_sub(cc[1], cv.p[1]), rn_sub(cc[2], cv.p[2])};
+    double t[3] = {rn_sub(rn_mul(cv.nu[1], w[2]), rn_mul(cv.nu[2], w[1])),
+                   rn_sub(rn_mul(cv.nu[2], w[0]), rn_mul(cv.nu[0], w[2])),
+                   rn_sub(rn_mul(cv.nu[0], w[1]), rn_mul(cv.nu[1], w[0]))};
+    const double m = rn_norm3(t);
+    for (int e = 0; e < 3; ++e) t[e] = rn_div(t[e], m);
+    const double bt = rn_dot3(z, t);
+    for (int e = 0; e < 3; ++e) z[e] = rn_sub(z[e], rn_mul(bt, t[e]));
+  }
 }
 
 // tie-resolved cp_{S-C}(x_j) for one curve (see the file comment)
@@ -327,6 +364,7 @@ cpm_status cpm_internal_set_boundary(cpm_ctx *c, const cpm_curve_desc *curves, i
     const cpm_curve_desc &s = curves[k];
     d.kind = s.kind; d.bc = s.bc; d.two_sided = s.two_sided; d.n_samples = s.n_samples;
     d.bc_minus = s.bc_minus ? s.bc_minus : s.bc;
+    d.projected = s.projected ? 1 : 0;
     for (int e = 0; e < 3; ++e) { d.p[e] = s.p[e]; d.nu[e] = s.nu[e]; d.ref[e] = s.ref[e]; }
     d.rad = s.rad;
     d.sample_off = off;

@@ -38,6 +38,7 @@
 struct CurveDev {
   int kind, bc, two_sided, n_samples;
   int bc_minus;        // BC type on the minus side (resolved: never 0)
+  int projected;       // projected crossing test (Sec. 4.7)
   double p[3], nu[3], ref[3], rad;
   int64_t sample_off;  // offset of this curve's samples in the concatenated layout
 };
