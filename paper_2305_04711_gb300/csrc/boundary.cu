@@ -339,6 +339,8 @@ void cpm_free_boundary(cpm_ctx *c) {
   cudaFree(c->d_spec_ecol); cudaFree(c->d_spec_ew); cudaFree(c->d_spec_ew32); cudaFree(c->d_spec_fcol);
   cpm_free_cells(c);
   cudaFree(c->d_T_ptr); cudaFree(c->d_T_row); cudaFree(c->d_cellid); cudaFree(c->d_w1d64); cudaFree(c->d_w1d32);
+  cudaFree(c->d_tblk);
+  c->d_tblk = nullptr;
   cudaFree(c->d_T_kind); cudaFree(c->d_T_val); cudaFree(c->d_T_val32);
   delete[] c->h_curves;
   c->h_curves = nullptr;

@@ -186,6 +186,7 @@ struct cpm_ctx {
   bool transpose_ready = false;
   int64_t nT = 0;                   // entries of the per-column remainder lists
   int32_t *d_cellid = nullptr;      // [nb*512] cell index of a packed base location, -1 if none
+  double *d_tblk = nullptr;         // [ncells][64] per-cell blocks of E^T b (one right-hand side; FP32 uses the front half)
   double *d_w1d64 = nullptr;        // [NS][12] per-axis Lagrange factors (transposed gather)
   float *d_w1d32 = nullptr;         // [NS][12]
   int32_t *d_T_ptr = nullptr;       // [N+1] CSR over columns

@@ -132,6 +132,7 @@ struct TArgs {
   const int32_t *T_src;
   const int32_t *T_kind;
   const T *T_val;
+  T *tblk;  // [ncells][64] per-cell blocks (one right-hand side), or nullptr
 };
 
 // b_c = s * sum of lambda over the rows whose unflipped FD slot points at c
@@ -159,6 +160,49 @@ __global__ void __launch_bounds__(256) tb_kernel(TArgs<T> A, T s, const T *__res
   }
 }
 
+// One right-hand side: per stencil cell the block of its E^T b contributions,
+// blk[cz*16 + cy*4 + cx] = sum over the cell's rows of w_x[cx] w_y[cy] w_z[cz] b_row,
+// one thread per cell (the cell's rows share the 4x4x4 node set); the node
+// gather below then reads one value per cell containing the node instead of
+// revisiting every row of it.
+template <typename T, int NP, int NZ>
+__global__ void __launch_bounds__(128) tcell_kernel(TArgs<T> A, int64_t ncells, const T *__restrict__ bv) {
+  for (int64_t cid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cid < ncells;
+       cid += (int64_t)gridDim.x * blockDim.x) {
+    T blk[NZ][NP][NP];
+#pragma unroll
+    for (int cz = 0; cz < NZ; ++cz)
+#pragma unroll
+      for (int cy = 0; cy < NP; ++cy)
+#pragma unroll
+        for (int cx = 0; cx < NP; ++cx) blk[cz][cy][cx] = T(0);
+    const int32_t q1 = __ldg(A.cell_start + cid + 1);
+    for (int32_t q = __ldg(A.cell_start + cid); q < q1; ++q) {
+      const int64_t row = __ldg(A.cell_rows + q);
+      const T *wr = A.w1d + row * 12;
+      const T bb = __ldg(bv + row);
+      T wx[NP], wy[NP], wz[NZ];
+#pragma unroll
+      for (int k = 0; k < NP; ++k) { wx[k] = __ldg(wr + k); wy[k] = __ldg(wr + 4 + k); }
+#pragma unroll
+      for (int k = 0; k < NZ; ++k) wz[k] = __ldg(wr + 8 + k);
+#pragma unroll
+      for (int cz = 0; cz < NZ; ++cz)
+#pragma unroll
+        for (int cy = 0; cy < NP; ++cy)
+#pragma unroll
+          for (int cx = 0; cx < NP; ++cx) blk[cz][cy][cx] += ((wx[cx] * wy[cy]) * wz[cz]) * bb;
+    }
+    T *out = A.tblk + cid * 64;
+#pragma unroll
+    for (int cz = 0; cz < NZ; ++cz)
+#pragma unroll
+      for (int cy = 0; cy < NP; ++cy)
+#pragma unroll
+        for (int cx = 0; cx < NP; ++cx) out[cz * 16 + cy * 4 + cx] = blk[cz][cy][cx];
+  }
+}
+
 // y = R (d lambda_S + E^T b + remainder)
 template <typename T>
 __global__ void __launch_bounds__(256) ty_kernel(TArgs<T> A, T dg, T s, T rowscale, T cs, const T *__restrict__ lam,
@@ -180,6 +224,11 @@ __global__ void __launch_bounds__(256) ty_kernel(TArgs<T> A, T dg, T s, T rowsca
             if (key < 0) continue;
             const int32_t cell = __ldg(A.cellid + key);
             if (cell < 0) continue;
+            if (A.tblk) {
+              // one right-hand side: the cell's block holds its rows' sum
+              acc += A.tblk[(int64_t)cell * 64 + cz * 16 + cy * 4 + cx];
+              continue;
+            }
             const int32_t q1 = __ldg(A.cell_start + cell + 1);
             for (int32_t q = __ldg(A.cell_start + cell); q < q1; ++q) {
               const int64_t row = __ldg(A.cell_rows + q);
@@ -206,8 +255,8 @@ __global__ void __launch_bounds__(256) ty_kernel(TArgs<T> A, T dg, T s, T rowsca
 cpm_status cpm_build_transpose(cpm_ctx *c) {
   cudaStream_t st = c->stream;
   cudaFree(c->d_T_ptr); cudaFree(c->d_T_row); cudaFree(c->d_T_kind); cudaFree(c->d_T_val); cudaFree(c->d_T_val32);
-  cudaFree(c->d_cellid); cudaFree(c->d_w1d64); cudaFree(c->d_w1d32);
-  c->d_w1d64 = nullptr; c->d_w1d32 = nullptr;
+  cudaFree(c->d_cellid); cudaFree(c->d_w1d64); cudaFree(c->d_w1d32); cudaFree(c->d_tblk);
+  c->d_w1d64 = nullptr; c->d_w1d32 = nullptr; c->d_tblk = nullptr;
   c->d_T_ptr = nullptr; c->d_T_row = nullptr; c->d_T_kind = nullptr; c->d_T_val = nullptr; c->d_T_val32 = nullptr;
   c->d_cellid = nullptr;
   c->transpose_ready = false;
@@ -225,6 +274,7 @@ cpm_status cpm_build_transpose(cpm_ctx *c) {
     if (e_) { rc = cpm_internal_cuda_err(e_); goto done; } \
   } while (0)
   TRY(cudaMalloc(&c->d_cellid, sizeof(int32_t) * std::max<int64_t>(nkeys, 1)));
+  TRY(cudaMalloc(&c->d_tblk, sizeof(double) * 64 * std::max<int64_t>(c->ncells, 1)));
   TRY(cudaMemsetAsync(c->d_cellid, 0xFF, sizeof(int32_t) * std::max<int64_t>(nkeys, 1), st));
   TRY(cudaMalloc(&c->d_w1d64, sizeof(double) * 12 * std::max<int64_t>(c->NS, 1)));
   TRY(cudaMalloc(&c->d_w1d32, sizeof(float) * 12 * std::max<int64_t>(c->NS, 1)));
@@ -286,11 +336,25 @@ cpm_status cpm_apply_transpose_rc_T(cpm_ctx *c, double m, double n, double rowsc
   const double inv_h2 = 1.0 / (c->h * c->h);
   const T s = T(n * inv_h2), dg = T(m + n * (-2.0 * c->dim * inv_h2));
   const int64_t N = c->NS + c->NC;
+  // one right-hand side: per-cell blocks of E^T b (reserved at set-up)
+  A.tblk = (nrhs == 1 && ld == 1 && c->d_tblk && c->ncells > 0) ? reinterpret_cast<T *>(c->d_tblk) : nullptr;
   cpm_prof_begin(c, st);
   tb_kernel<T><<<cpm_grid(c->NS * nrhs, 256), 256, 0, st>>>(A, T(s * T(colscale)), u, bv, nrhs, ld);
+  int launched = 2;
+  if (A.tblk) {
+    const unsigned gc = cpm_grid(c->ncells, 128);
+    if (c->dim == 3) {
+      if (c->p == 2) tcell_kernel<T, 3, 3><<<gc, 128, 0, st>>>(A, c->ncells, bv);
+      else tcell_kernel<T, 4, 4><<<gc, 128, 0, st>>>(A, c->ncells, bv);
+    } else {
+      if (c->p == 2) tcell_kernel<T, 3, 1><<<gc, 128, 0, st>>>(A, c->ncells, bv);
+      else tcell_kernel<T, 4, 1><<<gc, 128, 0, st>>>(A, c->ncells, bv);
+    }
+    ++launched;
+  }
   ty_kernel<T><<<cpm_grid(N * nrhs, 256), 256, 0, st>>>(A, dg, s, T(rowscale), T(colscale), u, bv, v, nrhs, ld);
   cpm_prof_end(c, st, c->NS * (int64_t)nrhs);
-  cpm_count_launches(c, 2);
+  cpm_count_launches(c, launched);
   CPM_CUDA_TRY(cudaGetLastError());
   return CPM_OK;
 }
