@@ -526,6 +526,13 @@ def run_ours(args):
             del u32, v32
         except Exception as e:  # reported, not required
             roof["error"] = str(e)
+        try:
+            # the FMA throughput this device sustains in registers (the derived
+            # peak above is the contract's denominator; this is its check)
+            from paper_2305_04711_gb300.cpm import measure_fma_peak
+            roof["measured_fma_peak"] = measure_fma_peak()
+        except Exception as e:  # reported, not required
+            roof["measured_fma_peak"] = {"error": str(e)}
         line["roofline"] = roof
         # accuracy: against the closed form, and FP32+refinement against FP64
         a = band.extend(x).cpu().numpy()

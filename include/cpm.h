@@ -385,6 +385,15 @@ cpm_status cpm_autotune(cpm_ctx *ctx, int nrhs, int64_t ld, int prec, cpm_tune_i
  * single_mode outside 0..2), STATE (before cpm_set_boundary). */
 cpm_status cpm_set_tune(cpm_ctx *ctx, int nrhs, int prec, const cpm_tune_info *info);
 
+/* Measured arithmetic peaks of the current device, the denominators of the
+ * products' rooflines (no counterpart in the paper): TFLOP/s of FP32 FMA
+ * instructions, of packed-pair FP32 FMAs (two per instruction) and of FP64 FMAs,
+ * from chains of independent FMAs in registers over 8 blocks of 256 threads per
+ * SM, timed with CUDA events on the default stream after one warm-up launch.
+ * Allocates and frees a small output buffer; synchronises the device's default
+ * stream.  Any pointer may be NULL.  Errors: CUDA. */
+cpm_status cpm_measure_fma_peak(double *fp32_tflops, double *fp32_pair_tflops, double *fp64_tflops);
+
 /* Diagnostics: counts of crossing-test flips that found no BC twin (Sec. 4.2;
  * zero on smooth geometry within interpolation reach) and of special rows. */
 cpm_status cpm_diagnostics(const cpm_ctx *ctx, int64_t *noflip_twin, int64_t *n_special_rows);

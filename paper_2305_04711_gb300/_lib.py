@@ -25,7 +25,7 @@ EXPORTS = ["cpm_band_build", "cpm_band_info", "cpm_export_band", "cpm_set_bounda
            "cpm_rhs", "cpm_apply", "cpm_apply_transpose", "cpm_extend", "cpm_solve", "cpm_solve_adjoint",
            "cpm_boundary_grad", "cpm_destroy", "cpm_status_str", "cpm_diagnostics", "cpm_profile",
            "cpm_apply_noalloc", "cpm_apply_noalloc_max_bytes", "cpm_surface_gradient", "cpm_surface_divergence",
-           "cpm_reserve", "cpm_autotune", "cpm_set_tune"]
+           "cpm_reserve", "cpm_autotune", "cpm_set_tune", "cpm_measure_fma_peak"]
 
 
 class ShapeDesc(ctypes.Structure):
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.cpm_reserve.argtypes = [P, i64, i]
     L.cpm_autotune.argtypes = [P, i, i64, i, ctypes.POINTER(TuneInfo), P]
     L.cpm_set_tune.argtypes = [P, i, i, ctypes.POINTER(TuneInfo)]
+    L.cpm_measure_fma_peak.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3
     for name in EXPORTS:
         if name not in ("cpm_destroy", "cpm_status_str", "cpm_apply_noalloc_max_bytes"):
             getattr(L, name).restype = ctypes.c_int

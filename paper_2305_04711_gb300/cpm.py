@@ -91,6 +91,15 @@ def curve_descs(curves: Sequence, n_samples: Optional[Sequence[int]] = None):
     return arr
 
 
+def measure_fma_peak() -> dict:
+    """cpm_measure_fma_peak: the device's FP32 (scalar and packed-pair) and FP64
+    FMA throughput in TFLOP/s."""
+    lib = L.load()
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    L.check(lib.cpm_measure_fma_peak(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "cpm_measure_fma_peak")
+    return {"fp32_fma_tflops": a.value, "fp32_pair_fma_tflops": b.value, "fp64_fma_tflops": c.value}
+
+
 class Band:
     """A band Omega(S) with its operator (one cpm_ctx)."""
 
