@@ -104,3 +104,50 @@ def test_projected_latitude_circles_keep_the_closed_form_and_order(oracle_mod, b
         same.append(abs(o.A(0.0, 1.0) - o2.A(0.0, 1.0)).max())
     assert abs(fit_order(hs, errs) - order) < 0.45, errs
     assert max(same) == 0.0, same
+
+
+def test_torus_meridian_vectors_lie_along_the_toroidal_direction(oracle_mod):
+    """A meridian phi = phi0 of the torus: its conormal in S is the toroidal
+    direction e_phi = (-sin phi0, cos phi0, 0) all along it."""
+    R, rt, p0 = 1.0, 0.4, 0.3
+    cv = ci.torus_meridian(p0, R, rt, ci.BC_DIR1)
+    cv.projected = True
+    h = 1 / 16
+    o = oracle_mod.Oracle(ci.torus(R, rt), h).set_curves([cv])
+    e_phi = np.array([-math.sin(p0), math.cos(p0), 0.0])
+    checked = 0
+    for i in np.nonzero(o.near_c >= 0)[0][::3]:
+        z = o.crossing_vector(0, int(i))
+        dphi = (math.atan2(o.cp[i, 1], o.cp[i, 0]) - p0 + math.pi) % (2 * math.pi) - math.pi
+        if abs(dphi) * R < 0.5 * h * h:
+            continue  # cp_S on C (Sec. 4.2 tie)
+        assert np.linalg.norm(np.cross(z, e_phi)) < 1e-12 * max(1.0, np.linalg.norm(z))
+        assert np.sign(np.dot(z, e_phi)) == np.sign(dphi)
+        checked += 1
+    assert checked > 50
+
+
+def test_bumpy_point_vectors_are_tangent_to_the_surface(oracle_mod):
+    """A point C on the bumpy sphere: only n_S is projected out, so every vector
+    is orthogonal to the level-set gradient at C (App. A)."""
+    sh = ci.bumpy_sphere(16, seed=0)
+    d = np.array([0.0, 0.6, 0.8])
+    c = d * float(ci.bumpy_radius(sh, d))
+    cv = ci.point_curve(tuple(c), ci.BC_DIR1)
+    cv.projected = True
+    h = 1 / 24
+    o = oracle_mod.Oracle(sh, h).set_curves([cv])
+    # the gradient of phi(x) = |x| - rho(x/|x|) at C by central differences
+    def phi(x):
+        return np.linalg.norm(x) - float(ci.bumpy_radius(sh, x / np.linalg.norm(x)))
+    eps = 1e-6
+    g = np.array([(phi(c + eps * e) - phi(c - eps * e)) / (2 * eps) for e in np.eye(3)])
+    n = g / np.linalg.norm(g)
+    checked = 0
+    for i in np.nonzero(o.near_c >= 0)[0]:
+        z = o.crossing_vector(0, int(i))
+        if np.linalg.norm(o.cp[i] - c) < 0.2 * h * h:
+            continue
+        assert abs(np.dot(z, n)) < 1e-8 * max(1.0, np.linalg.norm(z))
+        checked += 1
+    assert checked > 20
