@@ -313,7 +313,9 @@ cpm_status cpm_surface_divergence(cpm_ctx *ctx, const double *X_dev, double *b_d
  * its later work.  Allocates nothing: the workspace for ld must be reserved
  * (cpm_reserve; ld = 1 is reserved by cpm_set_boundary).  Synchronises the
  * internal stream.  stats may be NULL.  Errors: ARG, STATE, CAPACITY, CUDA,
- * BREAKDOWN, NOT_CONVERGED (x holds the last iterate). */
+ * BREAKDOWN, NOT_CONVERGED (x holds the last iterate), TIMEOUT (a bounded wait
+ * of the fused single right-hand side product, single_mode 2, gave up since
+ * the last check; the products since then are void). */
 cpm_status cpm_solve(cpm_ctx *ctx, double m, double n, const double *f_dev, double *x_dev, int nrhs, int64_t ld,
                      const cpm_solve_opts *opts, cpm_solve_stats *stats, void *stream);
 
@@ -356,7 +358,9 @@ typedef struct {
   int combine_warps_per_sm;  /* grid cap of the warp-per-row combine (0: default 64) */
   int vec_blocks_per_sm;     /* blocks of 512 threads per SM of the Krylov vector kernels (1, 2 or 4) */
   int single_mode;           /* single right-hand side product: 0 = per-cell gather then combine (default),
-                              * 1 = per-row gather then combine, 2 = fused persistent kernel */
+                              * 1 = per-row gather then combine, 2 = fused persistent kernel (its bounded
+                              * waits set a device flag if they give up, which the next solve reports
+                              * as CPM_ERR_TIMEOUT) */
   double product_ms;         /* one operator product with the chosen shapes */
   double product_ms_default; /* the same with the built-in defaults */
   double vector_ms;          /* one two-product reduction over [N][ld] with the chosen blocks */

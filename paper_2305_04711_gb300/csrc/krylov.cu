@@ -1082,6 +1082,15 @@ cpm_status solve_impl(cpm_ctx *c, bool adjoint, double m, double n, const double
   }
   cpm_status out = CPM_OK;
   if (!conv) out = broke ? CPM_ERR_BREAKDOWN : CPM_ERR_NOT_CONVERGED;
+  // a bounded wait of the fused single right-hand side product that gave up
+  // (its device flag; set-up leaves the flags clear) voids the products
+  unsigned herr = 0;
+  CPM_CUDA_TRY(cudaMemcpyAsync(&herr, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (herr & CPM_DEVERR_WAIT) {
+    CPM_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), st));
+    out = CPM_ERR_TIMEOUT;
+  }
   if (stats) {
     stats->iterations = iters;
     stats->refinements = refinements;
